@@ -1,0 +1,231 @@
+/*
+ * reach.h -- C ABI of the GB300 visited-state store and its reachability driver.
+ *
+ * The store is the lockless shared hash table of Laarman, van de Pol and Weber,
+ * "Boosting Multi-Core Reachability Performance with Shared Hash Tables"
+ * (Section 3): a single operation, find-or-put, over fixed-length int32 state
+ * vectors (Section 3.1), an open-addressing bucket array of memoised hashes with
+ * a write-busy bit (Section 3.2), states kept in a separate data array indexed
+ * like the buckets, walking-the-line probing followed by double hashing
+ * (Alg. "find-or-put", Alg. "Walking the (cache) line"), and CAS claiming of
+ * empty buckets.  The reachability driver is a level-synchronous breadth-first
+ * form of Alg. "Reachability analysis" (Section 2).
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev are device pointers (cudaMalloc'd or from a tensor
+ *     allocator); pointers named *_host are host pointers.  The library never
+ *     keeps a caller pointer after the call returns, except the memory block
+ *     handed to *_create_at, which the caller keeps alive until *_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Device work is enqueued on it and is asynchronous unless stated.
+ *   - The return value is an ht_status.  Argument errors return at once with
+ *     nothing enqueued.  Errors found on the device (table full, a write-busy
+ *     wait or a barrier that ran out of its iteration limit) are latched in a
+ *     device word and returned by ht_sync / the reach_* result calls.  No
+ *     device loop is unbounded: every wait has an iteration limit and reports
+ *     HT_ERR_TIMEOUT instead of hanging.
+ *   - A handle may be used from one host thread at a time.
+ */
+#ifndef PAPER_1004_2772_GB300_REACH_H
+#define PAPER_1004_2772_GB300_REACH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ht_status;
+enum {
+  HT_OK = 0,
+  HT_ERR_INVALID = 1, /* bad argument; nothing was enqueued */
+  HT_ERR_OOM = 2,     /* device allocation failed, or the caller's block is too small */
+  HT_ERR_FULL = 3,    /* a key found no empty bucket within max_rehash lines */
+  HT_ERR_TIMEOUT = 4, /* a bounded wait (write-busy bucket, level barrier) ran out */
+  HT_ERR_CUDA = 5,    /* a CUDA runtime call failed */
+  HT_ERR_LEVELS = 6   /* more BFS levels than the caller's level_sizes capacity */
+};
+
+/* Bucket word layout (Section 3.2, "hash memoization" and the write bit):
+ *   0            empty
+ *   bit 31       0 = write (data being written), 1 = done (data complete)
+ *   bits 0..30   memo = bits 33..63 of the 64-bit state hash, 0 mapped to 1.
+ * The bucket index of a key is the low log2_buckets bits of the same hash
+ * (Section 3.2, 2^n-sized table).  A used bucket never returns to empty and
+ * never changes its memo (Fig. "State diagram of buckets"). */
+#define HT_BUCKET_DONE 0x80000000u
+#define HT_BUCKET_MEMO 0x7FFFFFFFu
+
+/* Tunable layout and safety limits; 0 in any field selects the default. */
+typedef struct {
+  uint32_t line_buckets;  /* buckets walked per line before rehashing: 8, 16 or 32
+                             (32, 64 or 128 bytes); default 8 */
+  uint32_t max_rehash;    /* lines probed before HT_ERR_FULL; default min(lines, 4096) */
+  uint32_t max_spin;      /* polls of a write-busy bucket before HT_ERR_TIMEOUT; default 2^18 */
+  uint32_t block_threads; /* threads per block of the batch and expansion kernels; default 256 */
+  uint32_t dedup;         /* 1 = merge equal keys inside a warp before probing (batch API) */
+  uint32_t reserved;
+  uint64_t hash_seed;     /* seed of the table hash; default a fixed constant */
+} ht_params;
+
+/* ------------------------------------------------------------------------ */
+/* The table: find-or-put over a caller's batch of keys.                      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct ht ht_t;
+
+/* Device bytes needed by a table of 2^log2_buckets buckets for state vectors of
+ * state_words int32 words: 4 bytes per bucket, 16*ceil(state_words/4) bytes of
+ * data per bucket (rows padded to 16 bytes), plus a small header. */
+ht_status ht_bytes(int log2_buckets, int state_words, uint64_t* bytes);
+
+/* Create an empty table (Section 3.1: no allocation during operation; the
+ * whole table is claimed up front).  ht_create allocates with cudaMalloc;
+ * ht_create_at carves the table out of the caller's device block `mem_dev` of
+ * `mem_bytes` bytes (256-byte aligned, at least ht_bytes()).  log2_buckets in
+ * [4, 31], state_words in [1, 32].  `params` may be NULL.  Synchronous. */
+ht_status ht_create(int log2_buckets, int state_words, const ht_params* params, ht_t** out);
+ht_status ht_create_at(int log2_buckets, int state_words, const ht_params* params, void* mem_dev,
+                       uint64_t mem_bytes, ht_t** out);
+ht_status ht_destroy(ht_t* h);
+
+/* Empty the table and zero its counters and error word (enqueued on stream). */
+ht_status ht_clear(ht_t* h, void* stream);
+
+/* find-or-put of n keys (Alg. "find-or-put"), one thread per key.
+ *   keys_dev  n rows of state_words int32, row-major, contiguous
+ *   seen_dev  out, n bytes: 0 = the key was not in the table and this call
+ *             stored it, 1 = the key was already stored, 2 = error (see ht_sync)
+ *   idx_dev   out, n uint32: bucket index of the key; the key's vector is row
+ *             idx of the data array.  May be NULL.
+ * Among equal keys inside one batch exactly one gets seen = 0 when the key was
+ * new; all get the same idx.  Which of them is unspecified.  Enqueued on stream. */
+ht_status ht_find_or_put(ht_t* h, const int32_t* keys_dev, uint64_t n, uint8_t* seen_dev,
+                         uint32_t* idx_dev, void* stream);
+
+/* Wait for the stream and return the latched device error (HT_OK if none). */
+ht_status ht_sync(ht_t* h, void* stream);
+
+typedef struct {
+  uint64_t stored;      /* keys inserted since the last clear */
+  uint64_t busy_waits;  /* probes that found a memo-equal bucket still in the write state */
+  uint64_t rehashes;    /* lines probed after the first, summed over keys */
+  uint64_t capacity;    /* number of buckets */
+  uint32_t error;       /* latched device error */
+  uint32_t state_words;
+} ht_stats_t;
+
+/* Synchronises `stream`, then reads the counters. */
+ht_status ht_stats(ht_t* h, void* stream, ht_stats_t* out);
+
+/* Full scan of the bucket array: number of done buckets, number of buckets
+ * still in the write state (0 after every completed call), and the sum over
+ * done buckets of the fingerprint of their data row:
+ *   x = state_words; for each word w: x = sm(x ^ (uint32)w); fingerprint = x,
+ * sm(z) being one SplitMix64 output step (Steele, Lea, Flood 2014).
+ * Synchronous (waits on stream). */
+ht_status ht_scan(ht_t* h, void* stream, uint64_t* done, uint64_t* writing, uint64_t* digest);
+
+/* Copy rows idx_dev[0..n) of the data array to out_dev (n x state_words int32). */
+ht_status ht_gather(ht_t* h, const uint32_t* idx_dev, uint64_t n, int32_t* out_dev, void* stream);
+
+/* Device pointers to the bucket array (uint32[2^log2_buckets]) and data array
+ * (rows of 4*ceil(state_words/4) int32), for inspection. */
+ht_status ht_arrays(ht_t* h, uint32_t** buckets_dev, int32_t** data_dev, uint32_t* row_words);
+
+/* ------------------------------------------------------------------------ */
+/* Reachability (Alg. "Reachability analysis", level-synchronous BFS).        */
+/* ------------------------------------------------------------------------ */
+
+/* A model: P processes with local automata, S shared int32 variables, state
+ * vectors of W int32 words: v[0..P) local states, v[P..P+S) shared variables,
+ * v[P+S..W) padding kept at 0.  All pointers are HOST pointers.
+ * Edges of process p leaving local state s are edge_begin[b] .. edge_begin[b+1]
+ * with b = n_local[0] + ... + n_local[p-1] + s.  Edge e is enabled in v when
+ *   guard_var[e] < 0 or v[P + guard_var[e]] == guard_val[e], and
+ *   not (crit[p] >= 0 and edge_dst[e] == crit[p] and another process q has
+ *        crit[q] >= 0 and v[q] == crit[q]);
+ * firing it sets v[p] = edge_dst[e] and, when upd_var[e] >= 0,
+ * v[P + upd_var[e]] = upd_val[e].  Every enabled edge is one transition. */
+typedef struct {
+  int32_t n_procs;           /* P, >= 1 */
+  int32_t n_shared;          /* S, >= 0 */
+  int32_t state_words;       /* W, P + S <= W <= 32 */
+  int32_t n_edges;           /* E */
+  const int32_t* n_local;    /* [P], each in [1, 65535] */
+  const int32_t* crit;       /* [P], critical local state or -1 */
+  const int32_t* edge_begin; /* [sum(n_local) + 1], non-decreasing, edge_begin[0] = 0 */
+  const int32_t* edge_dst;   /* [E] */
+  const int32_t* guard_var;  /* [E], -1 or in [0, S) */
+  const int32_t* guard_val;  /* [E] */
+  const int32_t* upd_var;    /* [E], -1 or in [0, S) */
+  const int32_t* upd_val;    /* [E] */
+} reach_model;
+
+typedef struct {
+  uint64_t states;      /* |V| */
+  uint64_t transitions; /* enabled edges summed over V = find-or-put calls */
+  uint64_t deadlocks;   /* states with no enabled edge */
+  uint64_t digest;      /* sum over V of the fingerprint described at ht_scan */
+  uint64_t busy_waits;  /* write-busy "lock" hits (Section 4.3) */
+  uint64_t rehashes;
+  uint32_t n_levels;    /* BFS levels including level 0 = {init} */
+  ht_status status;
+} reach_result;
+
+enum {
+  REACH_PERSISTENT = 0, /* one cooperative launch runs every level (device-side level barrier) */
+  REACH_PER_LEVEL = 1   /* one launch per level; the host reads each level's size */
+};
+
+typedef struct reach_ctx reach_ctx_t;
+
+/* Device bytes of a context: a table of 2^log2_buckets buckets for states of up
+ * to max_state_words words, two frontier arrays of 2^log2_buckets uint32, a
+ * model area, counters and max_levels level sizes. */
+ht_status reach_ctx_bytes(int log2_buckets, int max_state_words, uint32_t max_levels,
+                          uint64_t* bytes);
+ht_status reach_ctx_create(int log2_buckets, int max_state_words, uint32_t max_levels,
+                           const ht_params* params, reach_ctx_t** out);
+ht_status reach_ctx_create_at(int log2_buckets, int max_state_words, uint32_t max_levels,
+                              const ht_params* params, void* mem_dev, uint64_t mem_bytes,
+                              reach_ctx_t** out);
+ht_status reach_ctx_destroy(reach_ctx_t* c);
+
+/* Validate the model and init (host) and upload both (enqueued on stream). */
+ht_status reach_ctx_load(reach_ctx_t* c, const reach_model* m, const int32_t* init_host,
+                         void* stream);
+
+/* Clear the table and explore from the loaded init.  REACH_PERSISTENT enqueues
+ * everything and returns without waiting; REACH_PER_LEVEL waits on the stream
+ * once per level.  Results stay on the device until reach_ctx_result. */
+ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream);
+
+/* Wait for the stream and copy the result (and up to max_levels level sizes,
+ * level_sizes_host may be NULL) to the host.  Returns out->status. */
+ht_status reach_ctx_result(reach_ctx_t* c, void* stream, uint64_t* level_sizes_host,
+                           uint32_t max_levels, reach_result* out);
+
+/* Device time of the last reach_ctx_run, from CUDA events recorded on its
+ * stream: kernel_ms spans the expansion kernel launch (persistent: the one
+ * cooperative launch; per-level: from the seed launch to the end of the last
+ * level launch, host gaps included), launches = kernels it launched.  Waits on
+ * the events. */
+ht_status reach_ctx_last_timing(reach_ctx_t* c, float* kernel_ms, uint32_t* launches);
+
+/* The context's table (owned by the context), for ht_scan / ht_gather. */
+ht_status reach_ctx_table(reach_ctx_t* c, ht_t** table);
+
+/* One-shot reach(model, init): load + run + result on `ctx`. */
+ht_status reach(reach_ctx_t* c, const reach_model* m, const int32_t* init_host, int mode,
+                void* stream, uint64_t* level_sizes_host, uint32_t max_levels, reach_result* out);
+
+/* Human-readable name of a status code (static storage). */
+const char* ht_status_string(ht_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAPER_1004_2772_GB300_REACH_H */

@@ -1,0 +1,424 @@
+"""Python binding of the C ABI in include/reach.h (ctypes; argument marshalling only).
+
+Every computation runs in the CUDA library libvss.so; this module converts
+arguments and raises on error codes.  It fails loudly when the library has not
+been built: there is no CPU fallback.
+
+Two layers:
+  * functions named exactly like the C entry points (ht_create, ht_find_or_put,
+    reach_ctx_run, reach, ...), taking raw pointers / ints;
+  * `Table` and `ReachContext`, which take device memory from PyTorch tensors
+    (torch is used for memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+HT_OK, HT_ERR_INVALID, HT_ERR_OOM, HT_ERR_FULL, HT_ERR_TIMEOUT, HT_ERR_CUDA, HT_ERR_LEVELS = range(7)
+REACH_PERSISTENT, REACH_PER_LEVEL = 0, 1
+STATUS_NAMES = {0: "HT_OK", 1: "HT_ERR_INVALID", 2: "HT_ERR_OOM", 3: "HT_ERR_FULL",
+                4: "HT_ERR_TIMEOUT", 5: "HT_ERR_CUDA", 6: "HT_ERR_LEVELS"}
+
+EXPORTED = [
+    "ht_bytes", "ht_create", "ht_create_at", "ht_destroy", "ht_clear", "ht_find_or_put", "ht_sync",
+    "ht_stats", "ht_scan", "ht_gather", "ht_arrays", "ht_status_string",
+    "reach_ctx_bytes", "reach_ctx_create", "reach_ctx_create_at", "reach_ctx_destroy",
+    "reach_ctx_load", "reach_ctx_run", "reach_ctx_result", "reach_ctx_table", "reach",
+    "reach_ctx_last_timing",
+]
+
+
+class HtError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: {STATUS_NAMES.get(self.status, self.status)}")
+
+
+class ht_params(ctypes.Structure):
+    _fields_ = [("line_buckets", ctypes.c_uint32), ("max_rehash", ctypes.c_uint32),
+                ("max_spin", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("dedup", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("hash_seed", ctypes.c_uint64)]
+
+
+class ht_stats_t(ctypes.Structure):
+    _fields_ = [("stored", ctypes.c_uint64), ("busy_waits", ctypes.c_uint64),
+                ("rehashes", ctypes.c_uint64), ("capacity", ctypes.c_uint64),
+                ("error", ctypes.c_uint32), ("state_words", ctypes.c_uint32)]
+
+
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+class reach_model(ctypes.Structure):
+    _fields_ = [("n_procs", ctypes.c_int32), ("n_shared", ctypes.c_int32),
+                ("state_words", ctypes.c_int32), ("n_edges", ctypes.c_int32),
+                ("n_local", _ip), ("crit", _ip), ("edge_begin", _ip), ("edge_dst", _ip),
+                ("guard_var", _ip), ("guard_val", _ip), ("upd_var", _ip), ("upd_val", _ip)]
+
+
+class reach_result(ctypes.Structure):
+    _fields_ = [("states", ctypes.c_uint64), ("transitions", ctypes.c_uint64),
+                ("deadlocks", ctypes.c_uint64), ("digest", ctypes.c_uint64),
+                ("busy_waits", ctypes.c_uint64), ("rehashes", ctypes.c_uint64),
+                ("n_levels", ctypes.c_uint32), ("status", ctypes.c_int32)]
+
+
+_lib = None
+_VP = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_i = ctypes.c_int
+_st = ctypes.c_int32
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libvss.so (built by __graft_entry__.build()); raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is not built; run __graft_entry__.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    sig = {
+        "ht_bytes": [_i, _i, ctypes.POINTER(_u64)],
+        "ht_create": [_i, _i, ctypes.POINTER(ht_params), ctypes.POINTER(_VP)],
+        "ht_create_at": [_i, _i, ctypes.POINTER(ht_params), _VP, _u64, ctypes.POINTER(_VP)],
+        "ht_destroy": [_VP],
+        "ht_clear": [_VP, _VP],
+        "ht_find_or_put": [_VP, _VP, _u64, _VP, _VP, _VP],
+        "ht_sync": [_VP, _VP],
+        "ht_stats": [_VP, _VP, ctypes.POINTER(ht_stats_t)],
+        "ht_scan": [_VP, _VP, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
+        "ht_gather": [_VP, _VP, _u64, _VP, _VP],
+        "ht_arrays": [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_VP), ctypes.POINTER(ctypes.c_uint32)],
+        "reach_ctx_bytes": [_i, _i, ctypes.c_uint32, ctypes.POINTER(_u64)],
+        "reach_ctx_create": [_i, _i, ctypes.c_uint32, ctypes.POINTER(ht_params), ctypes.POINTER(_VP)],
+        "reach_ctx_create_at": [_i, _i, ctypes.c_uint32, ctypes.POINTER(ht_params), _VP, _u64,
+                                ctypes.POINTER(_VP)],
+        "reach_ctx_destroy": [_VP],
+        "reach_ctx_load": [_VP, ctypes.POINTER(reach_model), _VP, _VP],
+        "reach_ctx_run": [_VP, _i, _VP],
+        "reach_ctx_result": [_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(reach_result)],
+        "reach_ctx_table": [_VP, ctypes.POINTER(_VP)],
+        "reach_ctx_last_timing": [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint32)],
+        "reach": [_VP, ctypes.POINTER(reach_model), _VP, _i, _VP, _VP, ctypes.c_uint32,
+                  ctypes.POINTER(reach_result)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = _st
+    L.ht_status_string.argtypes = [_st]
+    L.ht_status_string.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(status: int, what: str):
+    if status != HT_OK:
+        raise HtError(status, what)
+
+
+# ---------------------------------------------------------------------------
+# Same-name thin wrappers (raw pointers as ints, streams as ints).
+# ---------------------------------------------------------------------------
+
+def ht_bytes(log2_buckets: int, state_words: int) -> int:
+    out = _u64()
+    _check(load().ht_bytes(log2_buckets, state_words, ctypes.byref(out)), "ht_bytes")
+    return out.value
+
+
+def ht_create(log2_buckets: int, state_words: int, params: ht_params | None = None) -> int:
+    h = _VP()
+    _check(load().ht_create(log2_buckets, state_words, ctypes.byref(params) if params else None,
+                            ctypes.byref(h)), "ht_create")
+    return h.value
+
+
+def ht_create_at(log2_buckets, state_words, params, mem_dev: int, mem_bytes: int) -> int:
+    h = _VP()
+    _check(load().ht_create_at(log2_buckets, state_words, ctypes.byref(params) if params else None,
+                               mem_dev, mem_bytes, ctypes.byref(h)), "ht_create_at")
+    return h.value
+
+
+def ht_destroy(h: int) -> int:
+    return load().ht_destroy(h)
+
+
+def ht_clear(h: int, stream: int = 0) -> int:
+    return load().ht_clear(h, stream)
+
+
+def ht_find_or_put(h: int, keys_dev: int, n: int, seen_dev: int, idx_dev: int, stream: int = 0) -> int:
+    return load().ht_find_or_put(h, keys_dev, n, seen_dev, idx_dev, stream)
+
+
+def ht_sync(h: int, stream: int = 0) -> int:
+    return load().ht_sync(h, stream)
+
+
+def ht_stats(h: int, stream: int = 0) -> ht_stats_t:
+    s = ht_stats_t()
+    _check(load().ht_stats(h, stream, ctypes.byref(s)), "ht_stats")
+    return s
+
+
+def ht_scan(h: int, stream: int = 0) -> tuple[int, int, int]:
+    d, w, g = _u64(), _u64(), _u64()
+    _check(load().ht_scan(h, stream, ctypes.byref(d), ctypes.byref(w), ctypes.byref(g)), "ht_scan")
+    return d.value, w.value, g.value
+
+
+def ht_gather(h: int, idx_dev: int, n: int, out_dev: int, stream: int = 0) -> int:
+    return load().ht_gather(h, idx_dev, n, out_dev, stream)
+
+
+def ht_arrays(h: int) -> tuple[int, int, int]:
+    b, d, rw = _VP(), _VP(), ctypes.c_uint32()
+    _check(load().ht_arrays(h, ctypes.byref(b), ctypes.byref(d), ctypes.byref(rw)), "ht_arrays")
+    return b.value, d.value, rw.value
+
+
+def reach_ctx_bytes(log2_buckets: int, max_state_words: int, max_levels: int) -> int:
+    out = _u64()
+    _check(load().reach_ctx_bytes(log2_buckets, max_state_words, max_levels, ctypes.byref(out)),
+           "reach_ctx_bytes")
+    return out.value
+
+
+def reach_ctx_create_at(log2_buckets, max_state_words, max_levels, params, mem_dev, mem_bytes) -> int:
+    c = _VP()
+    _check(load().reach_ctx_create_at(log2_buckets, max_state_words, max_levels,
+                                      ctypes.byref(params) if params else None, mem_dev, mem_bytes,
+                                      ctypes.byref(c)), "reach_ctx_create_at")
+    return c.value
+
+
+def reach_ctx_create(log2_buckets, max_state_words, max_levels, params=None) -> int:
+    c = _VP()
+    _check(load().reach_ctx_create(log2_buckets, max_state_words, max_levels,
+                                   ctypes.byref(params) if params else None, ctypes.byref(c)),
+           "reach_ctx_create")
+    return c.value
+
+
+def reach_ctx_destroy(c: int) -> int:
+    return load().reach_ctx_destroy(c)
+
+
+class _ModelArgs:
+    """Keeps the numpy arrays of a model alive while the C struct points at them."""
+
+    def __init__(self, m):
+        as32 = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+        self.arrays = [as32(a) for a in (m.n_local, m.crit, m.edge_begin, m.edge_dst, m.guard_var,
+                                         m.guard_val, m.upd_var, m.upd_val)]
+        self.init = as32(m.init)
+        p = [a.ctypes.data_as(_ip) for a in self.arrays]
+        self.struct = reach_model(m.n_procs, m.n_shared, m.state_words, int(m.edge_dst.shape[0]), *p)
+
+
+def reach_ctx_load(c: int, model, stream: int = 0) -> int:
+    a = _ModelArgs(model)
+    return load().reach_ctx_load(c, ctypes.byref(a.struct), a.init.ctypes.data, stream)
+
+
+def reach_ctx_run(c: int, mode: int = REACH_PERSISTENT, stream: int = 0) -> int:
+    return load().reach_ctx_run(c, mode, stream)
+
+
+def reach_ctx_result(c: int, stream: int = 0, max_levels: int = 1 << 16):
+    levels = np.zeros(max_levels, dtype=np.uint64)
+    r = reach_result()
+    st = load().reach_ctx_result(c, stream, levels.ctypes.data, max_levels, ctypes.byref(r))
+    return st, r, levels[:min(r.n_levels, max_levels)].astype(np.int64)
+
+
+def reach_ctx_last_timing(c: int) -> tuple[float, int]:
+    ms, n = ctypes.c_float(), ctypes.c_uint32()
+    _check(load().reach_ctx_last_timing(c, ctypes.byref(ms), ctypes.byref(n)), "reach_ctx_last_timing")
+    return ms.value, n.value
+
+
+def reach_ctx_table(c: int) -> int:
+    t = _VP()
+    _check(load().reach_ctx_table(c, ctypes.byref(t)), "reach_ctx_table")
+    return t.value
+
+
+def reach(c: int, model, mode: int = REACH_PERSISTENT, stream: int = 0, max_levels: int = 1 << 16):
+    a = _ModelArgs(model)
+    levels = np.zeros(max_levels, dtype=np.uint64)
+    r = reach_result()
+    st = load().reach(c, ctypes.byref(a.struct), a.init.ctypes.data, mode, stream,
+                      levels.ctypes.data, max_levels, ctypes.byref(r))
+    return st, r, levels[:min(r.n_levels, max_levels)].astype(np.int64)
+
+
+# ---------------------------------------------------------------------------
+# Torch-backed convenience layer.
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def current_stream() -> int:
+    return _torch().cuda.current_stream().cuda_stream
+
+
+def make_params(**kw) -> ht_params:
+    p = ht_params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Table:
+    """A find-or-put table whose device memory is a torch uint8 tensor."""
+
+    def __init__(self, log2_buckets: int, state_words: int, device="cuda", **params):
+        torch = _torch()
+        self.log2_buckets, self.state_words = log2_buckets, state_words
+        self.params = make_params(**params)
+        nbytes = ht_bytes(log2_buckets, state_words)
+        self.mem = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.mem.data_ptr()
+        aligned = (base + 255) // 256 * 256
+        self.handle = ht_create_at(log2_buckets, state_words, self.params, aligned, nbytes)
+
+    def close(self):
+        if self.handle:
+            ht_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def clear(self):
+        _check(ht_clear(self.handle, current_stream()), "ht_clear")
+
+    def find_or_put(self, keys, want_idx: bool = True):
+        """keys: int32 CUDA tensor [n, state_words]. Returns (seen uint8, idx int32)."""
+        torch = _torch()
+        assert keys.is_cuda and keys.dtype == torch.int32 and keys.dim() == 2
+        assert keys.shape[1] == self.state_words and keys.is_contiguous()
+        n = keys.shape[0]
+        seen = torch.empty(n, dtype=torch.uint8, device=keys.device)
+        idx = torch.empty(n, dtype=torch.int32, device=keys.device) if want_idx else None
+        _check(ht_find_or_put(self.handle, keys.data_ptr(), n, seen.data_ptr(),
+                              idx.data_ptr() if idx is not None else 0, current_stream()),
+               "ht_find_or_put")
+        return seen, idx
+
+    def sync(self) -> int:
+        return ht_sync(self.handle, current_stream())
+
+    def stats(self) -> ht_stats_t:
+        return ht_stats(self.handle, current_stream())
+
+    def scan(self):
+        return ht_scan(self.handle, current_stream())
+
+    def gather(self, idx):
+        torch = _torch()
+        out = torch.empty((idx.shape[0], self.state_words), dtype=torch.int32, device=idx.device)
+        _check(ht_gather(self.handle, idx.data_ptr(), idx.shape[0], out.data_ptr(), current_stream()),
+               "ht_gather")
+        return out
+
+    def arrays(self):
+        """(buckets uint32 view as int32 tensor, data int32 tensor [nb, row_words])."""
+        torch = _torch()
+        b, d, rw = ht_arrays(self.handle)
+        nb = 1 << self.log2_buckets
+        base = self.mem.data_ptr()
+        buckets = self.mem[b - base:b - base + 4 * nb].view(torch.int32)
+        data = self.mem[d - base:d - base + 4 * nb * rw].view(torch.int32).view(nb, rw)
+        return buckets, data
+
+
+@dataclass
+class ReachOutput:
+    states: int
+    transitions: int
+    deadlocks: int
+    digest: int
+    level_sizes: list
+    busy_waits: int
+    rehashes: int
+    status: int
+
+
+class ReachContext:
+    """Device-resident reachability context (table + frontiers), memory from torch."""
+
+    def __init__(self, log2_buckets: int, max_state_words: int, max_levels: int = 1 << 14,
+                 device="cuda", **params):
+        torch = _torch()
+        self.log2_buckets, self.max_state_words, self.max_levels = log2_buckets, max_state_words, max_levels
+        self.params = make_params(**params)
+        nbytes = reach_ctx_bytes(log2_buckets, max_state_words, max_levels)
+        self.mem = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        aligned = (self.mem.data_ptr() + 255) // 256 * 256
+        self.handle = reach_ctx_create_at(log2_buckets, max_state_words, max_levels, self.params,
+                                          aligned, nbytes)
+
+    def close(self):
+        if self.handle:
+            reach_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def load(self, model):
+        _check(reach_ctx_load(self.handle, model, current_stream()), "reach_ctx_load")
+
+    def run(self, mode: int = REACH_PERSISTENT):
+        _check(reach_ctx_run(self.handle, mode, current_stream()), "reach_ctx_run")
+
+    def result(self, raise_on_error: bool = True) -> ReachOutput:
+        st, r, levels = reach_ctx_result(self.handle, current_stream(), self.max_levels)
+        if raise_on_error:
+            _check(st, "reach_ctx_result")
+        return ReachOutput(int(r.states), int(r.transitions), int(r.deadlocks), int(r.digest),
+                           [int(x) for x in levels], int(r.busy_waits), int(r.rehashes), int(st))
+
+    def reach(self, model, mode: int = REACH_PERSISTENT, raise_on_error: bool = True) -> ReachOutput:
+        st, r, levels = reach(self.handle, model, mode, current_stream(), self.max_levels)
+        if raise_on_error:
+            _check(st, "reach")
+        return ReachOutput(int(r.states), int(r.transitions), int(r.deadlocks), int(r.digest),
+                           [int(x) for x in levels], int(r.busy_waits), int(r.rehashes), int(st))
+
+    def last_timing(self) -> tuple[float, int]:
+        """(device ms of the last run's expansion kernels, kernels launched)."""
+        return reach_ctx_last_timing(self.handle)
+
+    def table_handle(self) -> int:
+        return reach_ctx_table(self.handle)
+
+    def scan(self):
+        return ht_scan(self.table_handle(), current_stream())

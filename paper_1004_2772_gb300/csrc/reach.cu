@@ -1,0 +1,724 @@
+// Level-synchronous reachability (Alg. "Reachability analysis") on the table.
+//
+// One thread expands one frontier state: it reads the state's row of the data
+// array, enumerates the enabled edges of the model (next-state), and calls
+// find-or-put on every successor.  A successor the table reports as new goes
+// to the next frontier (the paper's enqueue-on-not-seen; Alg. "Reachability
+// analysis" writes the test the other way round, but find-or-put answers
+// "seen").  New indices are staged in per-thread shared-memory slots and
+// appended with one atomicAdd per warp and frontier round, so the next
+// frontier is compacted without a separate pass.
+//
+// Two drivers share the expansion code:
+//   persistent  one cooperative launch runs all levels; blocks meet at a
+//               device-side barrier (bounded spin) between levels;
+//   per-level   one launch per level; the host reads the next level's size.
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+#include "table.cuh"
+
+namespace vss {
+
+constexpr int kSlots = 8;                  // staged new indices per thread per frontier state
+constexpr int kModelMaxWords = 1 << 15;    // model blob capacity (int32 words, 128 KiB)
+constexpr int kHdr = 16;                   // blob header words
+
+// Model blob (int32 words):
+//   [0] P  [1] S  [2] W  [3] n_local_total  [4] E  [5] crit_any
+//   [6] off_base [7] off_crit [8] off_eb [9] off_edges [10] off_uval [11] off_init
+//   [12] smem_words (words copied to shared memory: everything before off_init)
+// edges are int4 {dst, guard_var, guard_val, upd_var}; uval[e] = upd_val.
+struct SModel {
+  int P, S, W, crit_any;
+  const int* base;
+  const int* crit;
+  const int* eb;
+  const int4* edges;
+  const int* uval;
+};
+
+struct __align__(16) ReachTotals {
+  unsigned long long transitions;
+  unsigned long long deadlocks;
+  unsigned long long digest;
+  unsigned long long stored;
+  uint32_t counts[4];   // frontier sizes, rotating over 3 levels
+  uint32_t bar_count;
+  uint32_t bar_gen;
+  uint32_t n_levels;
+  uint32_t pad;
+};
+
+struct ReachDev {
+  const int* blob;
+  int smem_words;
+  uint32_t* frontier0;
+  uint32_t* frontier1;
+  uint32_t cap;               // entries per frontier array
+  ReachTotals* tot;
+  unsigned long long* level_sizes;
+  uint32_t max_levels;
+  uint32_t bar_spin;
+};
+
+struct Acc {
+  unsigned long long transitions = 0, deadlocks = 0, digest = 0, stored = 0;
+};
+
+__device__ __forceinline__ SModel load_model_smem(const ReachDev& rd, int* sm) {
+  for (int i = threadIdx.x; i < rd.smem_words; i += blockDim.x) sm[i] = __ldg(rd.blob + i);
+  __syncthreads();
+  SModel m;
+  m.P = sm[0];
+  m.S = sm[1];
+  m.W = sm[2];
+  m.crit_any = sm[5];
+  m.base = sm + sm[6];
+  m.crit = sm + sm[7];
+  m.eb = sm + sm[8];
+  m.edges = reinterpret_cast<const int4*>(sm + sm[9]);
+  m.uval = sm + sm[10];
+  return m;
+}
+
+template <int NV>
+__device__ __forceinline__ void vec_set(Vec<NV>& v, int i, uint32_t x) {
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    v.c[j].x = (4 * j + 0 == i) ? x : v.c[j].x;
+    v.c[j].y = (4 * j + 1 == i) ? x : v.c[j].y;
+    v.c[j].z = (4 * j + 2 == i) ? x : v.c[j].z;
+    v.c[j].w = (4 * j + 3 == i) ? x : v.c[j].w;
+  }
+}
+
+// Push one new index: to this thread's shared-memory slot, or straight to the
+// next frontier when the slots are full.
+__device__ __forceinline__ void stage_new(uint32_t* slots, uint32_t& nnew, uint32_t idx,
+                                          uint32_t* next, uint32_t* next_count, uint32_t cap,
+                                          DevCounters* ctr) {
+  if (nnew < kSlots) {
+    slots[nnew * blockDim.x + threadIdx.x] = idx;
+    ++nnew;
+  } else {
+    const uint32_t pos = atomicAdd(next_count, 1u);
+    if (pos < cap) next[pos] = idx;
+    else latch_error(ctr, HT_ERR_FULL);
+  }
+}
+
+// Expand one state: next-state, then find-or-put per successor.
+template <int NV, int L>
+__device__ __forceinline__ void expand_state(const TableView& t, const SModel& m, uint32_t idx,
+                                             Acc& acc, LocalCounters& lc, uint32_t* slots,
+                                             uint32_t& nnew, uint32_t* next, uint32_t* next_count,
+                                             uint32_t cap) {
+  Vec<NV> v;
+  load_row<NV>(t.data + (size_t)idx * NV, v);
+  const int P = m.P;
+  int ncrit = 0;
+  if (m.crit_any) {
+    for (int p = 0; p < P; ++p) {
+      const int c = m.crit[p];
+      ncrit += (c >= 0 && (int)vec_get(v, p) == c) ? 1 : 0;
+    }
+  }
+  uint32_t cnt = 0;
+  for (int p = 0; p < P; ++p) {
+    const int s = (int)vec_get(v, p);
+    const int b = m.base[p] + s;
+    const int cp = m.crit[p];
+    const int others = ncrit - ((cp >= 0 && s == cp) ? 1 : 0);
+    const int e_end = m.eb[b + 1];
+    for (int e = m.eb[b]; e < e_end; ++e) {
+      const int4 E = m.edges[e];
+      if (E.y >= 0 && (int)vec_get(v, P + E.y) != E.z) continue;  // guard
+      if (cp >= 0 && E.x == cp && others > 0) continue;            // mutex
+      Vec<NV> w = v;
+      vec_set(w, p, (uint32_t)E.x);
+      if (E.w >= 0) vec_set(w, P + E.w, (uint32_t)m.uval[e]);
+      ++cnt;
+      const uint64_t h = table_hash(w, t.state_words, t.seed);
+      uint32_t sidx = 0;
+      const int r = find_or_put<NV, L>(t, w, h, sidx, lc);
+      if (r == FOP_NEW) {
+        acc.digest += fingerprint(w, t.state_words);
+        acc.stored++;
+        stage_new(slots, nnew, sidx, next, next_count, cap, t.ctr);
+      } else if (r == FOP_ERR) {
+        acc.transitions += cnt;
+        return;
+      }
+    }
+  }
+  acc.transitions += cnt;
+  if (cnt == 0) acc.deadlocks++;
+}
+
+// One level: every warp takes 32 consecutive frontier entries per round; after
+// a round the warp appends its staged indices with one atomicAdd.
+template <int NV, int L>
+__device__ __forceinline__ void run_level(const TableView& t, const SModel& m, const uint32_t* cur,
+                                          uint32_t n_cur, uint32_t* next, uint32_t* next_count,
+                                          uint32_t cap, Acc& acc, LocalCounters& lc,
+                                          uint32_t* slots) {
+  const unsigned lane = lane_id();
+  const uint32_t wpb = blockDim.x >> 5;
+  const uint32_t warps = gridDim.x * wpb;
+  for (uint32_t base = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32u; base < n_cur;
+       base += warps * 32u) {
+    const uint32_t f = base + lane;
+    uint32_t nnew = 0;
+    if (f < n_cur) {
+      const uint32_t idx = __ldcg(cur + f);
+      expand_state<NV, L>(t, m, idx, acc, lc, slots, nnew, next, next_count, cap);
+    }
+    __syncwarp();
+    uint32_t incl = nnew;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if ((int)lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total) {
+      uint32_t wbase = 0;
+      if (lane == 31) wbase = atomicAdd(next_count, total);
+      wbase = __shfl_sync(0xffffffffu, wbase, 31);
+      uint32_t pos = wbase + incl - nnew;
+      for (uint32_t k = 0; k < nnew; ++k, ++pos) {
+        if (pos < cap) next[pos] = slots[k * blockDim.x + threadIdx.x];
+        else latch_error(t.ctr, HT_ERR_FULL);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void flush_acc(const TableView& t, const ReachDev& rd, Acc& acc,
+                                          LocalCounters& lc) {
+  const unsigned long long tr = warp_sum(acc.transitions);
+  const unsigned long long dl = warp_sum(acc.deadlocks);
+  const unsigned long long dg = warp_sum(acc.digest);
+  const unsigned long long st = warp_sum(acc.stored);
+  const uint32_t bw = warp_sum(lc.busy_waits);
+  const uint32_t rh = warp_sum(lc.rehashes);
+  if (lane_id() == 0) {
+    if (tr) atomicAdd(&rd.tot->transitions, tr);
+    if (dl) atomicAdd(&rd.tot->deadlocks, dl);
+    if (dg) atomicAdd(&rd.tot->digest, dg);
+    if (st) atomicAdd(&t.ctr->stored, st);
+    if (bw) atomicAdd(&t.ctr->busy_waits, (unsigned long long)bw);
+    if (rh) atomicAdd(&t.ctr->rehashes, (unsigned long long)rh);
+  }
+  acc = Acc();
+  lc = LocalCounters();
+}
+
+// Insert init (level 0).  Run by one thread.
+template <int NV, int L>
+__device__ void seed_init(const TableView& t, const ReachDev& rd, Acc& acc, LocalCounters& lc) {
+  const int* init = rd.blob + rd.blob[11];
+  Vec<NV> v;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v.c[j] = *reinterpret_cast<const uint4*>(init + 4 * j);
+  const uint64_t h = table_hash(v, t.state_words, t.seed);
+  uint32_t idx = 0;
+  const int r = find_or_put<NV, L>(t, v, h, idx, lc);
+  rd.tot->counts[1] = 0;
+  rd.tot->counts[2] = 0;
+  if (r == FOP_NEW) {
+    rd.frontier0[0] = idx;
+    rd.tot->counts[0] = 1;
+    rd.level_sizes[0] = 1;
+    rd.tot->n_levels = 1;
+    acc.digest += fingerprint(v, t.state_words);
+    acc.stored++;
+  } else {
+    rd.tot->counts[0] = 0;
+    if (r != FOP_ERR) latch_error(t.ctr, HT_ERR_INVALID);  // table was not empty
+  }
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
+// wait is bounded: after `limit` polls the barrier latches HT_ERR_TIMEOUT and
+// returns false; it also returns false as soon as any error is latched, so
+// every block leaves the kernel instead of waiting for one that already left.
+__device__ bool grid_barrier(const ReachDev& rd, DevCounters* ctr) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int good = 1;
+    const uint32_t gen = ld_acquire(&rd.tot->bar_gen);
+    fence_acq_rel();
+    const uint32_t arrived = atomicAdd(&rd.tot->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      st_relaxed(&rd.tot->bar_count, 0u);
+      st_release(&rd.tot->bar_gen, gen + 1);
+    } else {
+      uint32_t spins = 0, ns = 32;
+      while (ld_acquire(&rd.tot->bar_gen) == gen) {
+        if (ld_relaxed(&ctr->err) != 0) { good = 0; break; }
+        if (++spins > rd.bar_spin) { latch_error(ctr, HT_ERR_TIMEOUT); good = 0; break; }
+        __nanosleep(ns);
+        ns = ns < 1024 ? ns * 2 : ns;
+      }
+    }
+    if (ld_relaxed(&ctr->err) != 0) good = 0;
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int NV, int L>
+__global__ void __launch_bounds__(256) k_reach_persistent(TableView t, ReachDev rd) {
+  extern __shared__ int smem[];
+  const SModel m = load_model_smem(rd, smem);
+  uint32_t* slots = reinterpret_cast<uint32_t*>(smem + ((rd.smem_words + 3) & ~3));
+  Acc acc;
+  LocalCounters lc;
+  if (blockIdx.x == 0 && threadIdx.x == 0) seed_init<NV, L>(t, rd, acc, lc);
+  if (grid_barrier(rd, t.ctr)) {
+    uint32_t k = 0;
+    for (;;) {
+      const uint32_t n_cur = ld_relaxed(&rd.tot->counts[k % 3]);
+      const uint32_t* cur = (k & 1) ? rd.frontier1 : rd.frontier0;
+      uint32_t* next = (k & 1) ? rd.frontier0 : rd.frontier1;
+      run_level<NV, L>(t, m, cur, n_cur, next, &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc,
+                       slots);
+      if (blockIdx.x == 0 && threadIdx.x == 0) st_relaxed(&rd.tot->counts[(k + 2) % 3], 0u);
+      if (!grid_barrier(rd, t.ctr)) break;
+      const uint32_t n_next = ld_relaxed(&rd.tot->counts[(k + 1) % 3]);
+      if (n_next == 0) break;
+      ++k;
+      if (k >= rd.max_levels) {
+        if (threadIdx.x == 0) latch_error(t.ctr, HT_ERR_LEVELS);
+        break;
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        rd.level_sizes[k] = n_next;
+        rd.tot->n_levels = k + 1;
+      }
+    }
+  }
+  flush_acc(t, rd, acc, lc);
+}
+
+template <int NV, int L>
+__global__ void k_reach_seed(TableView t, ReachDev rd) {
+  Acc acc;
+  LocalCounters lc;
+  seed_init<NV, L>(t, rd, acc, lc);
+  if (acc.digest) atomicAdd(&rd.tot->digest, acc.digest);
+  if (acc.stored) atomicAdd(&t.ctr->stored, acc.stored);
+}
+
+template <int NV, int L>
+__global__ void __launch_bounds__(256) k_reach_level(TableView t, ReachDev rd, uint32_t k) {
+  extern __shared__ int smem[];
+  const SModel m = load_model_smem(rd, smem);
+  uint32_t* slots = reinterpret_cast<uint32_t*>(smem + ((rd.smem_words + 3) & ~3));
+  Acc acc;
+  LocalCounters lc;
+  const uint32_t n_cur = rd.tot->counts[k % 3];
+  const uint32_t* cur = (k & 1) ? rd.frontier1 : rd.frontier0;
+  uint32_t* next = (k & 1) ? rd.frontier0 : rd.frontier1;
+  run_level<NV, L>(t, m, cur, n_cur, next, &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc, slots);
+  flush_acc(t, rd, acc, lc);
+}
+
+// ---------------------------------------------------------------------------
+// Dispatch.
+// ---------------------------------------------------------------------------
+struct ReachKernels {
+  void (*persistent)(TableView, ReachDev);
+  void (*seed)(TableView, ReachDev);
+  void (*level)(TableView, ReachDev, uint32_t);
+};
+
+template <int NV, int L>
+static ReachKernels kernels_for() {
+  return {k_reach_persistent<NV, L>, k_reach_seed<NV, L>, k_reach_level<NV, L>};
+}
+
+template <int NV>
+static ReachKernels kernels_nv(int L) {
+  switch (L) {
+    case 8: return kernels_for<NV, 8>();
+    case 16: return kernels_for<NV, 16>();
+    default: return kernels_for<NV, 32>();
+  }
+}
+
+static ReachKernels pick_kernels(int nv, int L) {
+  switch (nv) {
+    case 1: return kernels_nv<1>(L);
+    case 2: return kernels_nv<2>(L);
+    case 3: return kernels_nv<3>(L);
+    case 4: return kernels_nv<4>(L);
+    case 5: return kernels_nv<5>(L);
+    case 6: return kernels_nv<6>(L);
+    case 7: return kernels_nv<7>(L);
+    default: return kernels_nv<8>(L);
+  }
+}
+
+static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace vss
+
+using namespace vss;
+
+struct reach_ctx {
+  ht_t table;
+  int log2_nb = 0;
+  int max_words = 0;
+  uint32_t max_levels = 0;
+  void* owned = nullptr;
+  int* blob = nullptr;                 // device
+  uint32_t* frontier0 = nullptr;
+  uint32_t* frontier1 = nullptr;
+  ReachTotals* tot = nullptr;
+  unsigned long long* level_sizes = nullptr;
+  ReachTotals* host_tot = nullptr;     // pinned
+  std::vector<int> host_blob;
+  int smem_words = 0;
+  bool loaded = false;
+  int last_mode = -1;
+  std::vector<unsigned long long> host_levels;  // per-level mode
+  ht_status host_status = HT_OK;
+  int coop = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  uint32_t last_launches = 0;
+};
+
+static uint64_t ctx_bytes(int log2_nb, int max_words, uint32_t max_levels) {
+  const uint64_t nb = 1ull << log2_nb;
+  return align_up(table_bytes(log2_nb, max_words), 256) + align_up(kModelMaxWords * 4ull, 256) +
+         2 * align_up(nb * 4, 256) + align_up(sizeof(ReachTotals), 256) +
+         align_up((uint64_t)max_levels * 8, 256);
+}
+
+static ht_status pack_model(const reach_model* m, const int32_t* init, int max_words,
+                            std::vector<int>& blob) {
+  if (!m || !init) return HT_ERR_INVALID;
+  const int P = m->n_procs, S = m->n_shared, W = m->state_words, E = m->n_edges;
+  if (P < 1 || S < 0 || W < P + S || W > max_words || E < 0) return HT_ERR_INVALID;
+  if (!m->n_local || !m->crit || !m->edge_begin) return HT_ERR_INVALID;
+  if (E > 0 && (!m->edge_dst || !m->guard_var || !m->guard_val || !m->upd_var || !m->upd_val))
+    return HT_ERR_INVALID;
+  long long nl_total = 0;
+  for (int p = 0; p < P; ++p) {
+    if (m->n_local[p] < 1 || m->n_local[p] > 65535) return HT_ERR_INVALID;
+    if (m->crit[p] < -1 || m->crit[p] >= m->n_local[p]) return HT_ERR_INVALID;
+    nl_total += m->n_local[p];
+  }
+  if (m->edge_begin[0] != 0 || m->edge_begin[nl_total] != E) return HT_ERR_INVALID;
+  for (long long i = 0; i < nl_total; ++i)
+    if (m->edge_begin[i + 1] < m->edge_begin[i]) return HT_ERR_INVALID;
+  {
+    long long b = 0;
+    for (int p = 0; p < P; ++p)
+      for (int s = 0; s < m->n_local[p]; ++s, ++b)
+        for (int e = m->edge_begin[b]; e < m->edge_begin[b + 1]; ++e) {
+          if (m->edge_dst[e] < 0 || m->edge_dst[e] >= m->n_local[p]) return HT_ERR_INVALID;
+          if (m->guard_var[e] < -1 || m->guard_var[e] >= S) return HT_ERR_INVALID;
+          if (m->upd_var[e] < -1 || m->upd_var[e] >= S) return HT_ERR_INVALID;
+        }
+  }
+  for (int p = 0; p < P; ++p)
+    if (init[p] < 0 || init[p] >= m->n_local[p]) return HT_ERR_INVALID;
+  for (int w = P + S; w < W; ++w)
+    if (init[w] != 0) return HT_ERR_INVALID;  // padding words stay 0
+  auto up4 = [](long long x) { return (x + 3) & ~3LL; };
+  const long long off_base = kHdr;
+  const long long off_crit = off_base + P;
+  const long long off_eb = off_crit + P;
+  const long long off_edges = up4(off_eb + nl_total + 1);
+  const long long off_uval = off_edges + 4LL * E;
+  const long long off_init = up4(off_uval + E);
+  const long long total = off_init + 4LL * ((W + 3) / 4);
+  if (total > kModelMaxWords) return HT_ERR_INVALID;
+  blob.assign((size_t)total, 0);
+  int crit_any = 0;
+  for (int p = 0; p < P; ++p) crit_any |= (m->crit[p] >= 0);
+  int hdr[kHdr] = {P, S, W, (int)nl_total, E, crit_any, (int)off_base, (int)off_crit, (int)off_eb,
+                   (int)off_edges, (int)off_uval, (int)off_init, (int)off_init, 0, 0, 0};
+  std::memcpy(blob.data(), hdr, sizeof(hdr));
+  long long acc = 0;
+  for (int p = 0; p < P; ++p) {
+    blob[off_base + p] = (int)acc;
+    acc += m->n_local[p];
+    blob[off_crit + p] = m->crit[p];
+  }
+  for (long long i = 0; i <= nl_total; ++i) blob[off_eb + i] = m->edge_begin[i];
+  for (int e = 0; e < E; ++e) {
+    blob[off_edges + 4LL * e + 0] = m->edge_dst[e];
+    blob[off_edges + 4LL * e + 1] = m->guard_var[e];
+    blob[off_edges + 4LL * e + 2] = m->guard_val[e];
+    blob[off_edges + 4LL * e + 3] = m->upd_var[e];
+    blob[off_uval + e] = m->upd_val[e];
+  }
+  for (int w = 0; w < W; ++w) blob[off_init + w] = init[w];
+  return HT_OK;
+}
+
+static ReachDev make_rd(reach_ctx_t* c) {
+  ReachDev rd;
+  rd.blob = c->blob;
+  rd.smem_words = c->smem_words;
+  rd.frontier0 = c->frontier0;
+  rd.frontier1 = c->frontier1;
+  rd.cap = (uint32_t)(1ull << c->log2_nb);
+  rd.tot = c->tot;
+  rd.level_sizes = c->level_sizes;
+  rd.max_levels = c->max_levels;
+  rd.bar_spin = 1u << 22;
+  return rd;
+}
+
+static size_t smem_bytes_for(reach_ctx_t* c, int threads) {
+  return (size_t)((c->smem_words + 3) & ~3) * 4 + (size_t)kSlots * threads * 4;
+}
+
+extern "C" {
+
+ht_status reach_ctx_bytes(int log2_buckets, int max_state_words, uint32_t max_levels,
+                          uint64_t* bytes) {
+  if (!bytes || log2_buckets < 4 || log2_buckets > 31 || max_state_words < 1 ||
+      max_state_words > 32 || max_levels < 1)
+    return HT_ERR_INVALID;
+  *bytes = ctx_bytes(log2_buckets, max_state_words, max_levels);
+  return HT_OK;
+}
+
+ht_status reach_ctx_create_at(int log2_buckets, int max_state_words, uint32_t max_levels,
+                              const ht_params* params, void* mem_dev, uint64_t mem_bytes,
+                              reach_ctx_t** out) {
+  if (!out) return HT_ERR_INVALID;
+  *out = nullptr;
+  uint64_t need = 0;
+  ht_status st = reach_ctx_bytes(log2_buckets, max_state_words, max_levels, &need);
+  if (st != HT_OK) return st;
+  if (!mem_dev || (reinterpret_cast<uintptr_t>(mem_dev) & 255u)) return HT_ERR_INVALID;
+  if (mem_bytes < need) return HT_ERR_OOM;
+  reach_ctx_t* c = new (std::nothrow) reach_ctx_t();
+  if (!c) return HT_ERR_OOM;
+  const uint64_t tb = align_up(table_bytes(log2_buckets, max_state_words), 256);
+  st = table_init_at(&c->table, log2_buckets, max_state_words, params, mem_dev, tb);
+  if (st != HT_OK) {
+    delete c;
+    return st;
+  }
+  const uint64_t nb = 1ull << log2_buckets;
+  char* p = static_cast<char*>(mem_dev) + tb;
+  c->blob = reinterpret_cast<int*>(p);
+  p += align_up(kModelMaxWords * 4ull, 256);
+  c->frontier0 = reinterpret_cast<uint32_t*>(p);
+  p += align_up(nb * 4, 256);
+  c->frontier1 = reinterpret_cast<uint32_t*>(p);
+  p += align_up(nb * 4, 256);
+  c->tot = reinterpret_cast<ReachTotals*>(p);
+  p += align_up(sizeof(ReachTotals), 256);
+  c->level_sizes = reinterpret_cast<unsigned long long*>(p);
+  c->log2_nb = log2_buckets;
+  c->max_words = max_state_words;
+  c->max_levels = max_levels;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaMallocHost(&c->host_tot, sizeof(ReachTotals)) != cudaSuccess ||
+      cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return HT_ERR_CUDA;
+  }
+  *out = c;
+  return HT_OK;
+}
+
+ht_status reach_ctx_create(int log2_buckets, int max_state_words, uint32_t max_levels,
+                           const ht_params* params, reach_ctx_t** out) {
+  uint64_t bytes = 0;
+  if (!out) return HT_ERR_INVALID;
+  *out = nullptr;
+  ht_status st = reach_ctx_bytes(log2_buckets, max_state_words, max_levels, &bytes);
+  if (st != HT_OK) return st;
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return HT_ERR_OOM;
+  }
+  st = reach_ctx_create_at(log2_buckets, max_state_words, max_levels, params, mem, bytes, out);
+  if (st != HT_OK) {
+    cudaFree(mem);
+    return st;
+  }
+  (*out)->owned = mem;
+  return HT_OK;
+}
+
+ht_status reach_ctx_destroy(reach_ctx_t* c) {
+  if (!c) return HT_ERR_INVALID;
+  if (c->host_tot) cudaFreeHost(c->host_tot);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->owned) cudaFree(c->owned);
+  delete c;
+  return HT_OK;
+}
+
+ht_status reach_ctx_last_timing(reach_ctx_t* c, float* kernel_ms, uint32_t* launches) {
+  if (!c || c->last_mode < 0) return HT_ERR_INVALID;
+  VSS_CUDA_TRY(cudaEventSynchronize(c->ev1));
+  float ms = 0.f;
+  VSS_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  if (kernel_ms) *kernel_ms = ms;
+  if (launches) *launches = c->last_launches;
+  return HT_OK;
+}
+
+ht_status reach_ctx_table(reach_ctx_t* c, ht_t** table) {
+  if (!c || !table) return HT_ERR_INVALID;
+  *table = &c->table;
+  return HT_OK;
+}
+
+ht_status reach_ctx_load(reach_ctx_t* c, const reach_model* m, const int32_t* init_host,
+                         void* stream) {
+  if (!c) return HT_ERR_INVALID;
+  ht_status st = pack_model(m, init_host, c->max_words, c->host_blob);
+  if (st != HT_OK) return st;
+  st = table_set_words(&c->table, m->state_words);
+  if (st != HT_OK) return st;
+  c->smem_words = c->host_blob[11];
+  if (smem_bytes_for(c, (int)c->table.params.block_threads) > 200 * 1024) return HT_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // synchronous w.r.t. the host buffer: the blob vector may change on the next load
+  VSS_CUDA_TRY(cudaMemcpyAsync(c->blob, c->host_blob.data(), c->host_blob.size() * 4,
+                               cudaMemcpyHostToDevice, s));
+  VSS_CUDA_TRY(cudaStreamSynchronize(s));
+  c->loaded = true;
+  return HT_OK;
+}
+
+ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
+  if (!c || !c->loaded) return HT_ERR_INVALID;
+  if (mode != REACH_PERSISTENT && mode != REACH_PER_LEVEL) return HT_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ht_status st = table_clear(&c->table, s);
+  if (st != HT_OK) return st;
+  VSS_CUDA_TRY(cudaMemsetAsync(c->tot, 0, sizeof(ReachTotals), s));
+  const int threads = (int)c->table.params.block_threads;
+  const size_t smem = smem_bytes_for(c, threads);
+  const ReachKernels ks = pick_kernels((int)c->table.view.nv, (int)c->table.params.line_buckets);
+  TableView tv = c->table.view;
+  ReachDev rd = make_rd(c);
+  c->last_mode = mode;
+  c->host_status = HT_OK;
+  if (mode == REACH_PERSISTENT) {
+    if (!c->coop) return HT_ERR_CUDA;
+    VSS_CUDA_TRY(cudaFuncSetAttribute(ks.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    int per_sm = 0;
+    VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.persistent, threads, smem));
+    if (per_sm < 1) return HT_ERR_INVALID;
+    const int blocks = per_sm * c->table.num_sms;
+    void* args[] = {&tv, &rd};
+    VSS_CUDA_TRY(cudaEventRecord(c->ev0, s));
+    VSS_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(ks.persistent), blocks,
+                                             threads, args, smem, s));
+    VSS_CUDA_TRY(cudaEventRecord(c->ev1, s));
+    c->last_launches = 1;
+    return HT_OK;
+  }
+  // per-level: one launch per level, the host reads each level's size
+  VSS_CUDA_TRY(cudaFuncSetAttribute(ks.level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.level, threads, smem));
+  if (per_sm < 1) return HT_ERR_INVALID;
+  VSS_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  ks.seed<<<1, 1, 0, s>>>(tv, rd);
+  VSS_CUDA_TRY(cudaGetLastError());
+  c->last_launches = 1;
+  c->host_levels.assign(1, 1);
+  uint32_t n_cur = 1;
+  for (uint32_t k = 0;; ++k) {
+    const uint64_t warps_needed = (n_cur + 31) / 32;
+    const uint64_t want = (warps_needed * 32 + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)per_sm * c->table.num_sms;
+    const int blocks = (int)std::max<uint64_t>(1, std::min(want, cap));
+    VSS_CUDA_TRY(cudaMemsetAsync(&c->tot->counts[(k + 1) % 3], 0, 4, s));
+    ks.level<<<blocks, threads, smem, s>>>(tv, rd, k);
+    VSS_CUDA_TRY(cudaGetLastError());
+    VSS_CUDA_TRY(cudaEventRecord(c->ev1, s));
+    c->last_launches++;
+    VSS_CUDA_TRY(cudaMemcpyAsync(c->host_tot, c->tot, sizeof(ReachTotals), cudaMemcpyDeviceToHost, s));
+    uint32_t err = 0;
+    VSS_CUDA_TRY(cudaMemcpyAsync(&c->host_tot->pad, &c->table.view.ctr->err, 4,
+                                 cudaMemcpyDeviceToHost, s));
+    VSS_CUDA_TRY(cudaStreamSynchronize(s));
+    err = c->host_tot->pad;
+    if (err) {
+      c->host_status = (ht_status)err;
+      break;
+    }
+    const uint32_t n_next = c->host_tot->counts[(k + 1) % 3];
+    if (n_next == 0) break;
+    if (c->host_levels.size() >= c->max_levels) {
+      c->host_status = HT_ERR_LEVELS;
+      break;
+    }
+    c->host_levels.push_back(n_next);
+    n_cur = n_next;
+  }
+  return HT_OK;
+}
+
+ht_status reach_ctx_result(reach_ctx_t* c, void* stream, uint64_t* level_sizes_host,
+                           uint32_t max_levels, reach_result* out) {
+  if (!c || !out) return HT_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::memset(out, 0, sizeof(*out));
+  DevCounters ctr;
+  VSS_CUDA_TRY(cudaMemcpyAsync(c->host_tot, c->tot, sizeof(ReachTotals), cudaMemcpyDeviceToHost, s));
+  VSS_CUDA_TRY(cudaStreamSynchronize(s));
+  VSS_CUDA_TRY(cudaMemcpy(&ctr, c->table.view.ctr, sizeof(ctr), cudaMemcpyDeviceToHost));
+  const ReachTotals& t = *c->host_tot;
+  out->transitions = t.transitions;
+  out->deadlocks = t.deadlocks;
+  out->digest = t.digest;
+  out->states = ctr.stored;
+  out->busy_waits = ctr.busy_waits;
+  out->rehashes = ctr.rehashes;
+  out->status = ctr.err ? (ht_status)ctr.err : c->host_status;
+  if (c->last_mode == REACH_PER_LEVEL) {
+    out->n_levels = (uint32_t)c->host_levels.size();
+    if (level_sizes_host)
+      for (uint32_t i = 0; i < out->n_levels && i < max_levels; ++i)
+        level_sizes_host[i] = c->host_levels[i];
+  } else {
+    out->n_levels = t.n_levels;
+    if (level_sizes_host && out->n_levels) {
+      const uint32_t n = std::min(out->n_levels, max_levels);
+      VSS_CUDA_TRY(cudaMemcpy(level_sizes_host, c->level_sizes, (size_t)n * 8, cudaMemcpyDeviceToHost));
+    }
+  }
+  if (out->status == HT_OK && level_sizes_host && out->n_levels > max_levels) out->status = HT_ERR_LEVELS;
+  return out->status;
+}
+
+ht_status reach(reach_ctx_t* c, const reach_model* m, const int32_t* init_host, int mode,
+                void* stream, uint64_t* level_sizes_host, uint32_t max_levels, reach_result* out) {
+  ht_status st = reach_ctx_load(c, m, init_host, stream);
+  if (st != HT_OK) return st;
+  st = reach_ctx_run(c, mode, stream);
+  if (st != HT_OK) return st;
+  return reach_ctx_result(c, stream, level_sizes_host, max_levels, out);
+}
+
+}  // extern "C"

@@ -1,0 +1,159 @@
+// find-or-put on the GPU (Alg. "find-or-put" with Alg. "Walking the (cache) line").
+//
+// One thread owns one key.  Memory-level parallelism, not warp cooperation, is
+// what bounds a random-access table on HBM: a thread per key keeps one
+// independent 32-byte bucket-sector request in flight per resident thread.
+//
+// Walk (Alg. "Walking the (cache) line", read as in its prose: the buckets of
+// the aligned line that holds `index`, visited cyclically from `index`):
+//   line  = index / L,  offset = index mod L,  walk = offset, offset+1, ...,
+//   L-1, 0, ..., offset-1 inside the line.
+// The line is read lazily one 32-byte sector (8 buckets) at a time, so a
+// 128-byte line costs one sector when the key resolves in its first sector.
+//
+// Sequential semantics (Alg. "find-or-put"): the thread acts on the FIRST
+// bucket in walk order that is empty or carries its memo:
+//   empty      -> CAS(empty -> <memo, write>); on success write Data[i], publish
+//                 <memo, done>, answer "new"; on failure re-evaluate the bucket
+//                 with the value the CAS returned.
+//   memo-equal -> wait (bounded) while the bucket is in the write state, then
+//                 compare Data[i] with the key: equal answers "seen", otherwise
+//                 the walk continues.
+// Sector words read before a CAS may be stale, which is safe: the only change
+// a bucket can undergo is empty -> write(memo) -> done(memo), so a stale
+// non-empty word is still correct and a stale empty word is corrected by the
+// CAS.  After the line: next line = (line + (2*memo + 1)) mod lines (double
+// hashing with an odd step over a power-of-two line count, Section 3.2).
+#pragma once
+
+#include "common.cuh"
+
+namespace vss {
+
+struct LocalCounters {
+  uint32_t busy_waits = 0;
+  uint32_t rehashes = 0;
+};
+
+// Memory ordering of the publish step (Section 3.3: the data write must not be
+// reordered before the claim, nor the done mark before the data write).  The
+// writer orders data stores before <memo, done> with a gpu-scope fence; a
+// reader that observed <memo, done> with a relaxed load performs an acquire
+// fence before reading the data row.
+template <int NV>
+__device__ __forceinline__ bool data_equal_after_done(const TableView& t, uint32_t i,
+                                                      const Vec<NV>& key, bool acquired) {
+  if (!acquired) fence_acq_rel();
+  Vec<NV> row;
+  load_row<NV>(t.data + (size_t)i * NV, row);
+  return vec_eq(row, key);
+}
+
+// Wait while bucket i is in the write state (bounded, with nanosleep backoff).
+// Returns false on timeout (error latched).
+__device__ __forceinline__ bool wait_done(const TableView& t, uint32_t i, uint32_t& b,
+                                          LocalCounters& lc) {
+  uint32_t spins = 0, ns = 32;
+  lc.busy_waits++;
+  while (!(b & kDone)) {
+    if (++spins > t.max_spin) {
+      latch_error(t.ctr, HT_ERR_TIMEOUT);
+      return false;
+    }
+    __nanosleep(ns);
+    ns = ns < 2048 ? ns * 2 : ns;
+    b = ld_acquire(t.buckets + i);
+  }
+  return true;
+}
+
+template <int NV, int L>
+__device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& key, uint64_t h,
+                                        uint32_t& out_idx, LocalCounters& lc) {
+  static_assert(L == 8 || L == 16 || L == 32, "line of 8, 16 or 32 buckets");
+  constexpr int NS = L / kSectorBuckets;  // sectors per line
+  const uint32_t memo = memo_of(h);
+  const uint32_t index = (uint32_t)h & t.nb_mask;
+  const uint32_t off = index & (L - 1);
+  const uint32_t s0 = off >> 3;          // first sector of the walk
+  const uint32_t p0 = off & 7;           // first position inside it
+  const uint32_t step = (memo << 1) | 1u;
+  uint32_t line = index / L;
+
+  for (uint32_t r = 0; r <= t.max_rehash; ++r) {
+    if (r) {
+      lc.rehashes++;
+      if ((r & 31) == 0 && ld_relaxed(&t.ctr->err) != 0) return FOP_ERR;  // another key failed
+      line = (line + step) & t.lines_mask;
+    }
+    const uint32_t line_base = line * L;
+    uint32_t first[8];  // words of sector s0, kept for the wrap-around part of the walk
+#pragma unroll 1
+    for (int v = 0; v <= NS; ++v) {
+      const uint32_t sec = (s0 + (uint32_t)v) & (NS - 1);
+      const uint32_t base = line_base + sec * 8;
+      uint32_t w[8];
+      if (v == 0 || v == NS) {
+        if (v == 0) {
+          const uint4 a = ld_relaxed_v4(t.buckets + base);
+          const uint4 b = ld_relaxed_v4(t.buckets + base + 4);
+          first[0] = a.x; first[1] = a.y; first[2] = a.z; first[3] = a.w;
+          first[4] = b.x; first[5] = b.y; first[6] = b.z; first[7] = b.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) w[k] = first[k];
+      } else {
+        const uint4 a = ld_relaxed_v4(t.buckets + base);
+        const uint4 b = ld_relaxed_v4(t.buckets + base + 4);
+        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+        w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+      }
+      // positions of this visit, in walk order = ascending inside the sector
+      uint32_t todo = (v == 0) ? (0xFFu << p0) & 0xFFu : (v == NS) ? (1u << p0) - 1u : 0xFFu;
+      while (todo) {
+        uint32_t cand = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          cand |= ((w[k] == 0u) | ((w[k] & kMemoMask) == memo) ? 1u : 0u) << k;
+        cand &= todo;
+        if (!cand) break;
+        const int pos = __ffs(cand) - 1;
+        const uint32_t i = base + pos;
+        uint32_t b = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b = (k == pos) ? w[k] : b;
+        bool acquired = false;
+        if (b == 0u) {
+          const uint32_t old = atomicCAS(t.buckets + i, 0u, memo);  // <memo, write>
+          if (old == 0u) {
+            uint4* row = t.data + (size_t)i * NV;
+#pragma unroll
+            for (int j = 0; j < NV; ++j) row[j] = key.c[j];
+            fence_acq_rel();                 // data before <memo, done>
+            st_relaxed(t.buckets + i, memo | kDone);
+            out_idx = i;
+            return FOP_NEW;
+          }
+          b = old;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) w[k] = (k == pos) ? old : w[k];
+        }
+        if ((b & kMemoMask) == memo) {
+          if (!(b & kDone)) {
+            if (!wait_done(t, i, b, lc)) return FOP_ERR;
+            acquired = true;
+          }
+          if (data_equal_after_done<NV>(t, i, key, acquired)) {
+            out_idx = i;
+            return FOP_SEEN;
+          }
+        }
+        todo &= ~((2u << pos) - 1u);  // this position is settled; continue the walk
+      }
+    }
+  }
+  latch_error(t.ctr, HT_ERR_FULL);
+  return FOP_ERR;
+}
+
+}  // namespace vss

@@ -1,0 +1,140 @@
+"""Reachability on the GPU against the oracle (through the C ABI).
+
+Bar: bit-exact states, transitions, deadlocks, per-level sizes and digest,
+plus the table invariants after every run (done buckets = states, no bucket
+left in the write state, table-scan digest = reported digest).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import hand_models, load_golden
+from paper_1004_2772_gb300 import synth
+from test_oracle_pins import TINY_BEEM
+
+pytestmark = pytest.mark.gpu
+
+MODES = [0, 1]  # REACH_PERSISTENT, REACH_PER_LEVEL
+
+
+def log2_for(states, lf=0.5):
+    return max(6, int(np.ceil(np.log2(max(states, 1) / lf))))
+
+
+def check(b, ctx, m, mode, ref=None):
+    ref = ref or oracle.reach(m)
+    got = ctx.reach(m, mode=mode)
+    assert got.status == b.HT_OK
+    assert got.states == ref.states
+    assert got.transitions == ref.transitions
+    assert got.deadlocks == ref.deadlocks
+    assert got.level_sizes == ref.level_sizes
+    assert got.digest == ref.digest
+    done, writing, digest = ctx.scan()
+    assert (done, writing, digest) == (ref.states, 0, ref.digest)
+    return got
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("L", [8, 16, 32])
+def test_tiny_interleaving(cuda_lib, mode, L):
+    m = synth.tiny_interleaving_model()
+    ctx = cuda_lib.ReachContext(18, 5, max_levels=256, line_buckets=L)
+    got = check(cuda_lib, ctx, m, mode)
+    assert got.states == 100000 and got.transitions == 1000000
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_hand_models(cuda_lib, mode):
+    ctx = cuda_lib.ReachContext(8, 8, max_levels=64)
+    for m, d in hand_models():
+        got = check(cuda_lib, ctx, m, mode)
+        assert got.states == d["states"] and got.level_sizes == d["level_sizes"]
+
+
+@pytest.mark.parametrize("kw", TINY_BEEM, ids=[f"seed{k['seed']}" for k in TINY_BEEM])
+def test_tiny_guarded_models(cuda_lib, kw):
+    m = synth.beem_shaped_model(**kw)
+    ctx = cuda_lib.ReachContext(12, m.state_words, max_levels=1024)
+    for mode in MODES:
+        check(cuda_lib, ctx, m, mode)
+
+
+@pytest.mark.parametrize("k", [3, 17, 42, 101, 200, 256])
+def test_batched_family_models(cuda_lib, k):
+    """Interleaving models with 8-32 words per state (every row shape)."""
+    m = [x for x in synth.batched_models(count=1, first_seed=k, lo=1e3, hi=2e5)][0]
+    ref = oracle.reach(m)
+    ctx = cuda_lib.ReachContext(log2_for(ref.states), m.state_words, max_levels=4096)
+    check(cuda_lib, ctx, m, 0, ref)
+
+
+@pytest.mark.parametrize("W", [13, 16, 24, 32])
+def test_guarded_model_row_shapes(cuda_lib, W):
+    m = synth.beem_shaped_model(3, n_procs=8, n_shared=3, state_words=W, n_lo=3, n_hi=5,
+                                update_pct=40)
+    ref = oracle.reach(m, max_states=3_000_000)
+    assert not ref.truncated
+    ctx = cuda_lib.ReachContext(log2_for(ref.states), W, max_levels=4096)
+    for mode in MODES:
+        check(cuda_lib, ctx, m, mode, ref)
+
+
+def test_repeated_runs_and_reload(cuda_lib):
+    ctx = cuda_lib.ReachContext(18, 16, max_levels=4096)
+    a = synth.tiny_interleaving_model()
+    b = synth.beem_shaped_model(4, n_procs=6, n_shared=2, state_words=10, update_pct=50)
+    ra, rb = oracle.reach(a), oracle.reach(b)
+    for _ in range(2):
+        check(cuda_lib, ctx, a, 0, ra)
+        check(cuda_lib, ctx, b, 0, rb)
+        check(cuda_lib, ctx, a, 1, ra)
+
+
+def test_table_too_small_reports_full(cuda_lib):
+    m = synth.tiny_interleaving_model()
+    ctx = cuda_lib.ReachContext(16, 5, max_levels=256)   # 65536 buckets < 10^5 states
+    for mode in MODES:
+        got = ctx.reach(m, mode=mode, raise_on_error=False)
+        assert got.status == cuda_lib.HT_ERR_FULL
+        done, writing, _ = ctx.scan()
+        assert writing == 0 and done <= 65536
+
+
+def test_level_capacity_reports_levels(cuda_lib):
+    m = synth.tiny_interleaving_model()
+    ctx = cuda_lib.ReachContext(18, 5, max_levels=5)
+    for mode in MODES:
+        got = ctx.reach(m, mode=mode, raise_on_error=False)
+        assert got.status == cuda_lib.HT_ERR_LEVELS
+
+
+def test_invalid_models_rejected(cuda_lib):
+    m = synth.tiny_interleaving_model()
+    ctx = cuda_lib.ReachContext(10, 8, max_levels=64)
+    bad = synth.tiny_interleaving_model()
+    bad.init = bad.init.copy()
+    bad.init[0] = 10                      # local state out of range
+    with pytest.raises(cuda_lib.HtError):
+        ctx.load(bad)
+    wide = synth.interleaving_model(1, [2] * 9, 9)   # 9 words > context maximum of 8
+    with pytest.raises(cuda_lib.HtError):
+        ctx.load(wide)
+    bad2 = synth.tiny_interleaving_model()
+    bad2.edge_dst = bad2.edge_dst.copy()
+    bad2.edge_dst[3] = 99                 # edge target out of range
+    with pytest.raises(cuda_lib.HtError):
+        ctx.load(bad2)
+    ctx.load(m)                           # a valid model still loads afterwards
+
+
+def test_beem_shaped_medium(cuda_lib):
+    """A guarded 12-process model of about a million states, both drivers."""
+    g = load_golden("beem_medium.json")
+    m = synth.beem_shaped_model(**g["model"])
+    ctx = cuda_lib.ReachContext(g["log2_buckets"], 16, max_levels=4096)
+    for mode in MODES:
+        got = ctx.reach(m, mode=mode)
+        assert (got.states, got.transitions, got.deadlocks, got.digest) == (
+            g["states"], g["transitions"], g["deadlocks"], int(g["digest"], 16))
+        assert got.level_sizes == g["level_sizes"]
