@@ -33,13 +33,21 @@ sys.path.insert(0, ROOT)
 from paper_1004_2772_gb300 import synth  # noqa: E402
 
 METRIC = "states/sec & find_or_put ops/sec on 1 GB300; fraction of HBM random-sector roofline"
-WORKLOAD = dict(seed=7, update_pct=40)  # BEEM-shaped: 12 procs, 4 shared vars, W=16
+# BEEM-shaped: 12 guarded processes, 4 shared vars in [0,4), mutex, W = 16
+WORKLOADS = {
+    "beem": (dict(seed=7, update_pct=40), 26),
+    "beem-medium": (dict(seed=7, update_pct=40), 24),
+    "tiny": (None, 18),
+}
 LOG2_BUCKETS = 26
 MAX_LEVELS = 1 << 14
 
 
-def workload_model():
-    return synth.beem_shaped_model(**WORKLOAD)
+def workload_model(name="beem"):
+    spec, _ = WORKLOADS[name]
+    if spec is None:
+        return synth.tiny_interleaving_model()
+    return synth.beem_shaped_model(**spec)
 
 
 def peaks():
@@ -178,7 +186,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     import oracle
-    model = workload_model()
+    model = workload_model(args.workload)
     sample = int(os.environ.get("BENCH_REF_SAMPLE", "1000000"))
     for _ in range(args.warmup):
         oracle.reach(model, max_states=sample // 4)
@@ -209,7 +217,11 @@ def main():
     ap.add_argument("--mode", default="persistent", choices=["persistent", "per-level"])
     ap.add_argument("--line-buckets", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="beem", choices=sorted(WORKLOADS))
+    ap.add_argument("--log2-buckets", type=int, default=0, help="0 = the workload's size")
     args = ap.parse_args()
+    global LOG2_BUCKETS
+    LOG2_BUCKETS = args.log2_buckets or WORKLOADS[args.workload][1]
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -222,7 +234,7 @@ def main():
     _build.build()
     binding.load()
 
-    model = workload_model()
+    model = workload_model(args.workload)
     mode = binding.REACH_PERSISTENT if args.mode == "persistent" else binding.REACH_PER_LEVEL
     ctx = binding.ReachContext(LOG2_BUCKETS, model.state_words, max_levels=MAX_LEVELS,
                                line_buckets=args.line_buckets)

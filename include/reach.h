@@ -182,8 +182,9 @@ enum {
 typedef struct reach_ctx reach_ctx_t;
 
 /* Device bytes of a context: a table of 2^log2_buckets buckets for states of up
- * to max_state_words words, two frontier arrays of 2^log2_buckets uint32, a
- * model area, counters and max_levels level sizes. */
+ * to max_state_words words, two frontier arrays of 2^log2_buckets state rows
+ * (16*ceil(max_state_words/4) bytes each), a model area, counters and
+ * 2*max_levels 64-bit level records. */
 ht_status reach_ctx_bytes(int log2_buckets, int max_state_words, uint32_t max_levels,
                           uint64_t* bytes);
 ht_status reach_ctx_create(int log2_buckets, int max_state_words, uint32_t max_levels,
@@ -214,12 +215,32 @@ ht_status reach_ctx_result(reach_ctx_t* c, void* stream, uint64_t* level_sizes_h
  * the events. */
 ht_status reach_ctx_last_timing(reach_ctx_t* c, float* kernel_ms, uint32_t* launches);
 
+/* Level start times of the last REACH_PERSISTENT run: level_ns_host[k] is the
+ * device %globaltimer (ns) when level k began (k = 0: after init was
+ * inserted).  Synchronises `stream`; *n_levels = entries written. */
+ht_status reach_ctx_level_ns(reach_ctx_t* c, void* stream, uint64_t* level_ns_host,
+                             uint32_t max_levels, uint32_t* n_levels);
+
 /* The context's table (owned by the context), for ht_scan / ht_gather. */
 ht_status reach_ctx_table(reach_ctx_t* c, ht_t** table);
 
 /* One-shot reach(model, init): load + run + result on `ctx`. */
 ht_status reach(reach_ctx_t* c, const reach_model* m, const int32_t* init_host, int mode,
                 void* stream, uint64_t* level_sizes_host, uint32_t max_levels, reach_result* out);
+
+/* ------------------------------------------------------------------------ */
+/* Measurement.                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Random-access probe (the roofline denominator of this random-access path):
+ * n_access accesses to uniformly random units of a device buffer of `bytes`
+ * bytes (256-byte aligned; its contents are overwritten), unit by mode:
+ *   0  read one 32-byte sector          1  read 64 bytes (two adjacent sectors)
+ *   2  write one 32-byte sector         3  32-bit atomicAdd (a sector RMW in L2)
+ * Every thread keeps 8 accesses in flight.  *ms = device time from CUDA events
+ * on `stream`.  Synchronous.  Use a buffer much larger than L2 (e.g. 16 GiB). */
+ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_access, int mode, void* stream,
+                           float* ms);
 
 /* Human-readable name of a status code (static storage). */
 const char* ht_status_string(ht_status s);

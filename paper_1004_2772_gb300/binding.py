@@ -30,7 +30,7 @@ EXPORTED = [
     "ht_stats", "ht_scan", "ht_gather", "ht_arrays", "ht_status_string",
     "reach_ctx_bytes", "reach_ctx_create", "reach_ctx_create_at", "reach_ctx_destroy",
     "reach_ctx_load", "reach_ctx_run", "reach_ctx_result", "reach_ctx_table", "reach",
-    "reach_ctx_last_timing",
+    "reach_ctx_last_timing", "reach_ctx_level_ns", "vss_probe_random",
 ]
 
 
@@ -113,6 +113,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "reach_ctx_result": [_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(reach_result)],
         "reach_ctx_table": [_VP, ctypes.POINTER(_VP)],
         "reach_ctx_last_timing": [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint32)],
+        "reach_ctx_level_ns": [_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)],
+        "vss_probe_random": [_VP, _u64, _u64, _i, _VP, ctypes.POINTER(ctypes.c_float)],
         "reach": [_VP, ctypes.POINTER(reach_model), _VP, _i, _VP, _VP, ctypes.c_uint32,
                   ctypes.POINTER(reach_result)],
     }
@@ -254,6 +256,14 @@ def reach_ctx_last_timing(c: int) -> tuple[float, int]:
     return ms.value, n.value
 
 
+def reach_ctx_level_ns(c: int, stream: int = 0, max_levels: int = 1 << 16) -> np.ndarray:
+    out = np.zeros(max_levels, dtype=np.uint64)
+    n = ctypes.c_uint32()
+    _check(load().reach_ctx_level_ns(c, stream, out.ctypes.data, max_levels, ctypes.byref(n)),
+           "reach_ctx_level_ns")
+    return out[:n.value].astype(np.int64)
+
+
 def reach_ctx_table(c: int) -> int:
     t = _VP()
     _check(load().reach_ctx_table(c, ctypes.byref(t)), "reach_ctx_table")
@@ -267,6 +277,31 @@ def reach(c: int, model, mode: int = REACH_PERSISTENT, stream: int = 0, max_leve
     st = load().reach(c, ctypes.byref(a.struct), a.init.ctypes.data, mode, stream,
                       levels.ctypes.data, max_levels, ctypes.byref(r))
     return st, r, levels[:min(r.n_levels, max_levels)].astype(np.int64)
+
+
+def vss_probe_random(buf_dev: int, nbytes: int, n_access: int, mode: int, stream: int = 0) -> float:
+    ms = ctypes.c_float()
+    _check(load().vss_probe_random(buf_dev, nbytes, n_access, mode, stream, ctypes.byref(ms)),
+           "vss_probe_random")
+    return ms.value
+
+
+PROBE_MODES = {0: "read 32 B", 1: "read 64 B", 2: "write 32 B", 3: "atomic 32-bit"}
+
+
+def random_access_rates(gib: int = 16, n_access: int = 1 << 28, device="cuda") -> dict:
+    """Random accesses per second for each probe mode over a `gib` GiB buffer."""
+    torch = _torch()
+    nbytes = gib << 30
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    ptr = (buf.data_ptr() + 255) // 256 * 256
+    out = {}
+    for mode in PROBE_MODES:
+        vss_probe_random(ptr, nbytes, n_access // 8, mode, current_stream())  # warm-up
+        ms = min(vss_probe_random(ptr, nbytes, n_access, mode, current_stream()) for _ in range(3))
+        out[mode] = n_access / (ms / 1e3)
+    del buf
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -416,6 +451,10 @@ class ReachContext:
     def last_timing(self) -> tuple[float, int]:
         """(device ms of the last run's expansion kernels, kernels launched)."""
         return reach_ctx_last_timing(self.handle)
+
+    def level_ns(self) -> np.ndarray:
+        """Device timestamps (ns) of the level starts of the last persistent run."""
+        return reach_ctx_level_ns(self.handle, current_stream(), self.max_levels)
 
     def table_handle(self) -> int:
         return reach_ctx_table(self.handle)

@@ -5,9 +5,10 @@
 // find-or-put on every successor.  A successor the table reports as new goes
 // to the next frontier (the paper's enqueue-on-not-seen; Alg. "Reachability
 // analysis" writes the test the other way round, but find-or-put answers
-// "seen").  New indices are staged in per-thread shared-memory slots and
-// appended with one atomicAdd per warp and frontier round, so the next
-// frontier is compacted without a separate pass.
+// "seen").  Frontiers hold the state vectors themselves, so a level reads its
+// states with coalesced loads instead of a dependent gather through the data
+// array; new states are appended with one atomicAdd per warp and iteration,
+// so the next frontier is compacted without a separate pass.
 //
 // Two drivers share the expansion code:
 //   persistent  one cooperative launch runs all levels; blocks meet at a
@@ -23,7 +24,10 @@
 
 namespace vss {
 
-constexpr int kSlots = 8;                  // staged new indices per thread per frontier state
+constexpr int kDescCap = 1024;
+#ifndef VSS_REACH_MINB
+#define VSS_REACH_MINB 1  // __launch_bounds__ minimum resident blocks of the expansion kernels
+#endif             // successor descriptors per warp and round
 constexpr int kModelMaxWords = 1 << 15;    // model blob capacity (int32 words, 128 KiB)
 constexpr int kHdr = 16;                   // blob header words
 
@@ -31,9 +35,16 @@ constexpr int kHdr = 16;                   // blob header words
 //   [0] P  [1] S  [2] W  [3] n_local_total  [4] E  [5] crit_any
 //   [6] off_base [7] off_crit [8] off_eb [9] off_edges [10] off_uval [11] off_init
 //   [12] smem_words (words copied to shared memory: everything before off_init)
+//   [13] maxfan = sum over processes of the largest out-degree (bound on a state's successors)
+//   [14] spw_max = states per warp round, min(32, kDescCap / maxfan)
 // edges are int4 {dst, guard_var, guard_val, upd_var}; uval[e] = upd_val.
+template <int NV>
+__host__ __device__ constexpr int row_stride() { return 4 * NV + 4; }  // padded: conflict-free 16 B reads
+
+__host__ __device__ constexpr int warp_smem_words_nv(int nv) { return 32 * (4 * nv + 4) + kDescCap + 32; }
+
 struct SModel {
-  int P, S, W, crit_any;
+  int P, S, W, crit_any, maxfan, spw_max;
   const int* base;
   const int* crit;
   const int* eb;
@@ -47,6 +58,7 @@ struct __align__(16) ReachTotals {
   unsigned long long digest;
   unsigned long long stored;
   uint32_t counts[4];   // frontier sizes, rotating over 3 levels
+  uint32_t cursor[4];   // next unclaimed frontier row of a level, rotating over 3 levels
   uint32_t bar_count;
   uint32_t bar_gen;
   uint32_t n_levels;
@@ -56,14 +68,21 @@ struct __align__(16) ReachTotals {
 struct ReachDev {
   const int* blob;
   int smem_words;
-  uint32_t* frontier0;
-  uint32_t* frontier1;
-  uint32_t cap;               // entries per frontier array
+  uint4* frontier0;           // frontier rows (state vectors, nv chunks each)
+  uint4* frontier1;
+  uint32_t cap;               // rows per frontier array
   ReachTotals* tot;
   unsigned long long* level_sizes;
+  unsigned long long* level_ns;   // globaltimer at the start of each level (persistent driver)
   uint32_t max_levels;
   uint32_t bar_spin;
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 struct Acc {
   unsigned long long transitions = 0, deadlocks = 0, digest = 0, stored = 0;
@@ -77,6 +96,8 @@ __device__ __forceinline__ SModel load_model_smem(const ReachDev& rd, int* sm) {
   m.S = sm[1];
   m.W = sm[2];
   m.crit_any = sm[5];
+  m.maxfan = sm[13];
+  m.spw_max = sm[14];
   m.base = sm + sm[6];
   m.crit = sm + sm[7];
   m.eb = sm + sm[8];
@@ -96,105 +117,130 @@ __device__ __forceinline__ void vec_set(Vec<NV>& v, int i, uint32_t x) {
   }
 }
 
-// Push one new index: to this thread's shared-memory slot, or straight to the
-// next frontier when the slots are full.
-__device__ __forceinline__ void stage_new(uint32_t* slots, uint32_t& nnew, uint32_t idx,
-                                          uint32_t* next, uint32_t* next_count, uint32_t cap,
-                                          DevCounters* ctr) {
-  if (nnew < kSlots) {
-    slots[nnew * blockDim.x + threadIdx.x] = idx;
-    ++nnew;
-  } else {
-    const uint32_t pos = atomicAdd(next_count, 1u);
-    if (pos < cap) next[pos] = idx;
-    else latch_error(ctr, HT_ERR_FULL);
-  }
-}
-
-// Expand one state: next-state, then find-or-put per successor.
+// One level, warp-cooperatively and load-balanced over successors.
+//
+// A warp claims `spw` consecutive frontier states per round from a level
+// cursor (spw shrinks on small levels so that every warp gets work).  Phase 1: lane i < spw reads
+// state i's row, keeps it in shared memory, and lists the enabled edges of the
+// state (next-state) as descriptors (edge | process << 24) in its own slice
+// of the warp's descriptor area; it counts the state's transitions and, when
+// there are none, a deadlock.  A warp scan of the counts gives T successors.
+// Phase 2: lane j, j+32, ... builds successor j from its owner's row and the
+// descriptor, and runs find-or-put -- so no lane serialises a whole fan-out.
+// New indices are staged per lane and appended with one atomicAdd per round.
 template <int NV, int L>
-__device__ __forceinline__ void expand_state(const TableView& t, const SModel& m, uint32_t idx,
-                                             Acc& acc, LocalCounters& lc, uint32_t* slots,
-                                             uint32_t& nnew, uint32_t* next, uint32_t* next_count,
-                                             uint32_t cap) {
-  Vec<NV> v;
-  load_row<NV>(t.data + (size_t)idx * NV, v);
-  const int P = m.P;
-  int ncrit = 0;
-  if (m.crit_any) {
-    for (int p = 0; p < P; ++p) {
-      const int c = m.crit[p];
-      ncrit += (c >= 0 && (int)vec_get(v, p) == c) ? 1 : 0;
-    }
-  }
-  uint32_t cnt = 0;
-  for (int p = 0; p < P; ++p) {
-    const int s = (int)vec_get(v, p);
-    const int b = m.base[p] + s;
-    const int cp = m.crit[p];
-    const int others = ncrit - ((cp >= 0 && s == cp) ? 1 : 0);
-    const int e_end = m.eb[b + 1];
-    for (int e = m.eb[b]; e < e_end; ++e) {
-      const int4 E = m.edges[e];
-      if (E.y >= 0 && (int)vec_get(v, P + E.y) != E.z) continue;  // guard
-      if (cp >= 0 && E.x == cp && others > 0) continue;            // mutex
-      Vec<NV> w = v;
-      vec_set(w, p, (uint32_t)E.x);
-      if (E.w >= 0) vec_set(w, P + E.w, (uint32_t)m.uval[e]);
-      ++cnt;
-      const uint64_t h = table_hash(w, t.state_words, t.seed);
-      uint32_t sidx = 0;
-      const int r = find_or_put<NV, L>(t, w, h, sidx, lc);
-      if (r == FOP_NEW) {
-        acc.digest += fingerprint(w, t.state_words);
-        acc.stored++;
-        stage_new(slots, nnew, sidx, next, next_count, cap, t.ctr);
-      } else if (r == FOP_ERR) {
-        acc.transitions += cnt;
-        return;
-      }
-    }
-  }
-  acc.transitions += cnt;
-  if (cnt == 0) acc.deadlocks++;
-}
-
-// One level: every warp takes 32 consecutive frontier entries per round; after
-// a round the warp appends its staged indices with one atomicAdd.
-template <int NV, int L>
-__device__ __forceinline__ void run_level(const TableView& t, const SModel& m, const uint32_t* cur,
-                                          uint32_t n_cur, uint32_t* next, uint32_t* next_count,
-                                          uint32_t cap, Acc& acc, LocalCounters& lc,
-                                          uint32_t* slots) {
+__device__ __forceinline__ void run_level(const TableView& t, const SModel& m, const uint4* cur,
+                                          uint32_t n_cur, uint32_t* cursor, uint4* next,
+                                          uint32_t* next_count, uint32_t cap, Acc& acc,
+                                          LocalCounters& lc, uint32_t* wsm) {
+  constexpr int RS = row_stride<NV>();
+  uint32_t* rows = wsm;
+  uint32_t* desc = wsm + 32 * RS;
+  uint32_t* pref = desc + kDescCap;
   const unsigned lane = lane_id();
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t warps = gridDim.x * wpb;
-  for (uint32_t base = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32u; base < n_cur;
-       base += warps * 32u) {
-    const uint32_t f = base + lane;
-    uint32_t nnew = 0;
-    if (f < n_cur) {
-      const uint32_t idx = __ldcg(cur + f);
-      expand_state<NV, L>(t, m, idx, acc, lc, slots, nnew, next, next_count, cap);
+  uint32_t spw = (n_cur + warps - 1) / warps;
+  spw = spw < 1u ? 1u : (spw > (uint32_t)m.spw_max ? (uint32_t)m.spw_max : spw);
+  const int P = m.P;
+  const int maxfan = m.maxfan;
+  for (;;) {
+    // rounds are claimed dynamically, so warps that finish early take more
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(cursor, spw);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (base >= n_cur) break;
+    // ---- phase 1: expand the round's states into successor descriptors
+    uint32_t c = 0;
+    const uint64_t f = (uint64_t)base + lane;
+    if (lane < spw && f < n_cur) {
+      uint4* r = reinterpret_cast<uint4*>(rows + lane * RS);
+#pragma unroll
+      for (int j = 0; j < NV; ++j) r[j] = __ldcg(cur + f * NV + j);
+      const int* rw = reinterpret_cast<const int*>(rows + lane * RS);
+      int ncrit = 0;
+      if (m.crit_any) {
+        for (int p = 0; p < P; ++p) {
+          const int cp = m.crit[p];
+          ncrit += (cp >= 0 && rw[p] == cp) ? 1 : 0;
+        }
+      }
+      uint32_t* d = desc + lane * maxfan;
+      for (int p = 0; p < P; ++p) {
+        const int s = rw[p];
+        const int b = m.base[p] + s;
+        const int cp = m.crit[p];
+        const int others = ncrit - ((cp >= 0 && s == cp) ? 1 : 0);
+        const int e_end = m.eb[b + 1];
+        for (int e = m.eb[b]; e < e_end; ++e) {
+          const int4 E = m.edges[e];
+          if (E.y >= 0 && rw[P + E.y] != E.z) continue;      // guard
+          if (cp >= 0 && E.x == cp && others > 0) continue;  // mutex
+          d[c++] = (uint32_t)e | ((uint32_t)p << 24);
+        }
+      }
+      acc.transitions += c;
+      if (c == 0) acc.deadlocks++;
     }
-    __syncwarp();
-    uint32_t incl = nnew;
+    uint32_t incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
       if ((int)lane >= o) incl += y;
     }
-    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    if (total) {
-      uint32_t wbase = 0;
-      if (lane == 31) wbase = atomicAdd(next_count, total);
-      wbase = __shfl_sync(0xffffffffu, wbase, 31);
-      uint32_t pos = wbase + incl - nnew;
-      for (uint32_t k = 0; k < nnew; ++k, ++pos) {
-        if (pos < cap) next[pos] = slots[k * blockDim.x + threadIdx.x];
-        else latch_error(t.ctr, HT_ERR_FULL);
+    pref[lane] = incl;
+    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    // ---- phase 2: one successor per lane per iteration; new states are
+    // appended to the next frontier (rows) with one atomicAdd per warp and
+    // iteration, straight from registers
+    const uint32_t iters = (T + 31) / 32;
+    for (uint32_t it = 0; it < iters; ++it) {
+      const uint32_t j = it * 32 + lane;
+      bool is_new = false;
+      Vec<NV> w;
+      if (j < T) {
+        uint32_t o = 0;  // owner = first lane whose inclusive prefix exceeds j
+#pragma unroll
+        for (uint32_t step = 16; step > 0; step >>= 1)
+          if (pref[o + step - 1] <= j) o += step;
+        const uint32_t k = j - (o ? pref[o - 1] : 0u);
+        const uint32_t dd = desc[o * maxfan + k];
+        const int e = (int)(dd & 0xFFFFFFu);
+        const int p = (int)(dd >> 24);
+        const int4 E = m.edges[e];
+        const uint4* r = reinterpret_cast<const uint4*>(rows + o * RS);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) w.c[q] = r[q];
+        vec_set(w, p, (uint32_t)E.x);
+        if (E.w >= 0) vec_set(w, P + E.w, (uint32_t)m.uval[e]);
+        const uint64_t h = table_hash(w, t.state_words, t.seed);
+        uint32_t sidx = 0;
+        const int res = find_or_put<NV, L>(t, w, h, sidx, lc);
+        if (res == FOP_NEW) {
+          is_new = true;
+          acc.digest += fingerprint(w, t.state_words);
+          acc.stored++;
+        }
+      }
+      const unsigned nb = __ballot_sync(0xffffffffu, is_new);
+      if (nb) {
+        uint32_t wbase = 0;
+        if (lane == 0) wbase = atomicAdd(next_count, (uint32_t)__popc(nb));
+        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+        if (is_new) {
+          const uint32_t pos = wbase + __popc(nb & ((1u << lane) - 1u));
+          if (pos < cap) {
+            uint4* dst = next + (size_t)pos * NV;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) dst[q] = w.c[q];
+          } else {
+            latch_error(t.ctr, HT_ERR_FULL);
+          }
+        }
       }
     }
+    __syncwarp();  // the warp's shared rows/descriptors are rewritten next round
   }
 }
 
@@ -231,7 +277,8 @@ __device__ void seed_init(const TableView& t, const ReachDev& rd, Acc& acc, Loca
   rd.tot->counts[1] = 0;
   rd.tot->counts[2] = 0;
   if (r == FOP_NEW) {
-    rd.frontier0[0] = idx;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) rd.frontier0[j] = v.c[j];
     rd.tot->counts[0] = 1;
     rd.level_sizes[0] = 1;
     rd.tot->n_levels = 1;
@@ -264,7 +311,7 @@ __device__ bool grid_barrier(const ReachDev& rd, DevCounters* ctr) {
         if (ld_relaxed(&ctr->err) != 0) { good = 0; break; }
         if (++spins > rd.bar_spin) { latch_error(ctr, HT_ERR_TIMEOUT); good = 0; break; }
         __nanosleep(ns);
-        ns = ns < 1024 ? ns * 2 : ns;
+        ns = ns < 256 ? ns * 2 : ns;
       }
     }
     if (ld_relaxed(&ctr->err) != 0) good = 0;
@@ -275,22 +322,29 @@ __device__ bool grid_barrier(const ReachDev& rd, DevCounters* ctr) {
 }
 
 template <int NV, int L>
-__global__ void __launch_bounds__(256) k_reach_persistent(TableView t, ReachDev rd) {
+__global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_persistent(TableView t, ReachDev rd) {
   extern __shared__ int smem[];
   const SModel m = load_model_smem(rd, smem);
-  uint32_t* slots = reinterpret_cast<uint32_t*>(smem + ((rd.smem_words + 3) & ~3));
+  uint32_t* wsm = reinterpret_cast<uint32_t*>(smem + ((rd.smem_words + 3) & ~3)) +
+                  (threadIdx.x >> 5) * warp_smem_words_nv(NV);
   Acc acc;
   LocalCounters lc;
-  if (blockIdx.x == 0 && threadIdx.x == 0) seed_init<NV, L>(t, rd, acc, lc);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    seed_init<NV, L>(t, rd, acc, lc);
+    rd.level_ns[0] = global_ns();
+  }
   if (grid_barrier(rd, t.ctr)) {
     uint32_t k = 0;
     for (;;) {
       const uint32_t n_cur = ld_relaxed(&rd.tot->counts[k % 3]);
-      const uint32_t* cur = (k & 1) ? rd.frontier1 : rd.frontier0;
-      uint32_t* next = (k & 1) ? rd.frontier0 : rd.frontier1;
-      run_level<NV, L>(t, m, cur, n_cur, next, &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc,
-                       slots);
-      if (blockIdx.x == 0 && threadIdx.x == 0) st_relaxed(&rd.tot->counts[(k + 2) % 3], 0u);
+      const uint4* cur = (k & 1) ? rd.frontier1 : rd.frontier0;
+      uint4* next = (k & 1) ? rd.frontier0 : rd.frontier1;
+      run_level<NV, L>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next,
+                       &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc, wsm);
+      if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st_relaxed(&rd.tot->counts[(k + 2) % 3], 0u);
+        st_relaxed(&rd.tot->cursor[(k + 2) % 3], 0u);
+      }
       if (!grid_barrier(rd, t.ctr)) break;
       const uint32_t n_next = ld_relaxed(&rd.tot->counts[(k + 1) % 3]);
       if (n_next == 0) break;
@@ -301,6 +355,7 @@ __global__ void __launch_bounds__(256) k_reach_persistent(TableView t, ReachDev 
       }
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         rd.level_sizes[k] = n_next;
+        rd.level_ns[k] = global_ns();
         rd.tot->n_levels = k + 1;
       }
     }
@@ -318,16 +373,18 @@ __global__ void k_reach_seed(TableView t, ReachDev rd) {
 }
 
 template <int NV, int L>
-__global__ void __launch_bounds__(256) k_reach_level(TableView t, ReachDev rd, uint32_t k) {
+__global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_level(TableView t, ReachDev rd, uint32_t k) {
   extern __shared__ int smem[];
   const SModel m = load_model_smem(rd, smem);
-  uint32_t* slots = reinterpret_cast<uint32_t*>(smem + ((rd.smem_words + 3) & ~3));
+  uint32_t* wsm = reinterpret_cast<uint32_t*>(smem + ((rd.smem_words + 3) & ~3)) +
+                  (threadIdx.x >> 5) * warp_smem_words_nv(NV);
   Acc acc;
   LocalCounters lc;
   const uint32_t n_cur = rd.tot->counts[k % 3];
-  const uint32_t* cur = (k & 1) ? rd.frontier1 : rd.frontier0;
-  uint32_t* next = (k & 1) ? rd.frontier0 : rd.frontier1;
-  run_level<NV, L>(t, m, cur, n_cur, next, &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc, slots);
+  const uint4* cur = (k & 1) ? rd.frontier1 : rd.frontier0;
+  uint4* next = (k & 1) ? rd.frontier0 : rd.frontier1;
+  run_level<NV, L>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next, &rd.tot->counts[(k + 1) % 3],
+                   rd.cap, acc, lc, wsm);
   flush_acc(t, rd, acc, lc);
 }
 
@@ -380,10 +437,11 @@ struct reach_ctx {
   uint32_t max_levels = 0;
   void* owned = nullptr;
   int* blob = nullptr;                 // device
-  uint32_t* frontier0 = nullptr;
-  uint32_t* frontier1 = nullptr;
+  uint4* frontier0 = nullptr;
+  uint4* frontier1 = nullptr;
   ReachTotals* tot = nullptr;
   unsigned long long* level_sizes = nullptr;
+  unsigned long long* level_ns = nullptr;
   ReachTotals* host_tot = nullptr;     // pinned
   std::vector<int> host_blob;
   int smem_words = 0;
@@ -396,11 +454,14 @@ struct reach_ctx {
   uint32_t last_launches = 0;
 };
 
+static uint64_t frontier_bytes(int log2_nb, int max_words) {
+  return align_up((1ull << log2_nb) * 16ull * (uint64_t)((max_words + 3) / 4), 256);
+}
+
 static uint64_t ctx_bytes(int log2_nb, int max_words, uint32_t max_levels) {
-  const uint64_t nb = 1ull << log2_nb;
   return align_up(table_bytes(log2_nb, max_words), 256) + align_up(kModelMaxWords * 4ull, 256) +
-         2 * align_up(nb * 4, 256) + align_up(sizeof(ReachTotals), 256) +
-         align_up((uint64_t)max_levels * 8, 256);
+         2 * frontier_bytes(log2_nb, max_words) + align_up(sizeof(ReachTotals), 256) +
+         2 * align_up((uint64_t)max_levels * 8, 256);
 }
 
 static ht_status pack_model(const reach_model* m, const int32_t* init, int max_words,
@@ -446,8 +507,21 @@ static ht_status pack_model(const reach_model* m, const int32_t* init, int max_w
   blob.assign((size_t)total, 0);
   int crit_any = 0;
   for (int p = 0; p < P; ++p) crit_any |= (m->crit[p] >= 0);
+  long long maxfan = 0;
+  {
+    long long b = 0;
+    for (int p = 0; p < P; ++p) {
+      long long mp = 0;
+      for (int s = 0; s < m->n_local[p]; ++s, ++b)
+        mp = std::max<long long>(mp, m->edge_begin[b + 1] - m->edge_begin[b]);
+      maxfan += mp;
+    }
+  }
+  if (maxfan > kDescCap) return HT_ERR_INVALID;  // more successors per state than a warp round holds
+  const int fan = (int)std::max<long long>(1, maxfan);
+  const int spw_max = std::min(32, kDescCap / fan);
   int hdr[kHdr] = {P, S, W, (int)nl_total, E, crit_any, (int)off_base, (int)off_crit, (int)off_eb,
-                   (int)off_edges, (int)off_uval, (int)off_init, (int)off_init, 0, 0, 0};
+                   (int)off_edges, (int)off_uval, (int)off_init, (int)off_init, fan, spw_max, 0};
   std::memcpy(blob.data(), hdr, sizeof(hdr));
   long long acc = 0;
   for (int p = 0; p < P; ++p) {
@@ -476,13 +550,15 @@ static ReachDev make_rd(reach_ctx_t* c) {
   rd.cap = (uint32_t)(1ull << c->log2_nb);
   rd.tot = c->tot;
   rd.level_sizes = c->level_sizes;
+  rd.level_ns = c->level_ns;
   rd.max_levels = c->max_levels;
   rd.bar_spin = 1u << 22;
   return rd;
 }
 
 static size_t smem_bytes_for(reach_ctx_t* c, int threads) {
-  return (size_t)((c->smem_words + 3) & ~3) * 4 + (size_t)kSlots * threads * 4;
+  return (size_t)((c->smem_words + 3) & ~3) * 4 +
+         (size_t)(threads / 32) * warp_smem_words_nv((int)c->table.view.nv) * 4;
 }
 
 extern "C" {
@@ -514,17 +590,19 @@ ht_status reach_ctx_create_at(int log2_buckets, int max_state_words, uint32_t ma
     delete c;
     return st;
   }
-  const uint64_t nb = 1ull << log2_buckets;
   char* p = static_cast<char*>(mem_dev) + tb;
   c->blob = reinterpret_cast<int*>(p);
   p += align_up(kModelMaxWords * 4ull, 256);
-  c->frontier0 = reinterpret_cast<uint32_t*>(p);
-  p += align_up(nb * 4, 256);
-  c->frontier1 = reinterpret_cast<uint32_t*>(p);
-  p += align_up(nb * 4, 256);
+  const uint64_t fb = frontier_bytes(log2_buckets, max_state_words);
+  c->frontier0 = reinterpret_cast<uint4*>(p);
+  p += fb;
+  c->frontier1 = reinterpret_cast<uint4*>(p);
+  p += fb;
   c->tot = reinterpret_cast<ReachTotals*>(p);
   p += align_up(sizeof(ReachTotals), 256);
   c->level_sizes = reinterpret_cast<unsigned long long*>(p);
+  p += align_up((uint64_t)max_levels * 8, 256);
+  c->level_ns = reinterpret_cast<unsigned long long*>(p);
   c->log2_nb = log2_buckets;
   c->max_words = max_state_words;
   c->max_levels = max_levels;
@@ -579,6 +657,19 @@ ht_status reach_ctx_last_timing(reach_ctx_t* c, float* kernel_ms, uint32_t* laun
   VSS_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
   if (kernel_ms) *kernel_ms = ms;
   if (launches) *launches = c->last_launches;
+  return HT_OK;
+}
+
+ht_status reach_ctx_level_ns(reach_ctx_t* c, void* stream, uint64_t* level_ns_host,
+                             uint32_t max_levels, uint32_t* n_levels) {
+  if (!c || !level_ns_host || c->last_mode != REACH_PERSISTENT) return HT_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  VSS_CUDA_TRY(cudaStreamSynchronize(s));
+  uint32_t n = 0;
+  VSS_CUDA_TRY(cudaMemcpy(&n, &c->tot->n_levels, 4, cudaMemcpyDeviceToHost));
+  n = std::min(n, max_levels);
+  if (n) VSS_CUDA_TRY(cudaMemcpy(level_ns_host, c->level_ns, (size_t)n * 8, cudaMemcpyDeviceToHost));
+  if (n_levels) *n_levels = n;
   return HT_OK;
 }
 
@@ -653,6 +744,7 @@ ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
     const uint64_t cap = (uint64_t)per_sm * c->table.num_sms;
     const int blocks = (int)std::max<uint64_t>(1, std::min(want, cap));
     VSS_CUDA_TRY(cudaMemsetAsync(&c->tot->counts[(k + 1) % 3], 0, 4, s));
+    VSS_CUDA_TRY(cudaMemsetAsync(&c->tot->cursor[k % 3], 0, 4, s));
     ks.level<<<blocks, threads, smem, s>>>(tv, rd, k);
     VSS_CUDA_TRY(cudaGetLastError());
     VSS_CUDA_TRY(cudaEventRecord(c->ev1, s));

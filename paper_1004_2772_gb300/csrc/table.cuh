@@ -30,6 +30,24 @@
 
 namespace vss {
 
+// How a probe orders its read of a data row after the <memo, done> bucket
+// word it observed (Section 3.3 memory-model requirement):
+//   1 (default): bucket sectors are read with gpu-scope acquire loads, so
+//                every later load of the thread is ordered after them;
+//   0:           bucket sectors are read relaxed and an acquire fence is
+//                issued before a data row is compared.
+#ifndef VSS_ACQ_MODE
+#define VSS_ACQ_MODE 1
+#endif
+
+__device__ __forceinline__ uint4 ld_bucket_v4(const uint32_t* p) {
+#if VSS_ACQ_MODE == 1
+  return ld_acquire_v4(p);
+#else
+  return ld_relaxed_v4(p);
+#endif
+}
+
 struct LocalCounters {
   uint32_t busy_waits = 0;
   uint32_t rehashes = 0;
@@ -38,8 +56,9 @@ struct LocalCounters {
 // Memory ordering of the publish step (Section 3.3: the data write must not be
 // reordered before the claim, nor the done mark before the data write).  The
 // writer orders data stores before <memo, done> with a gpu-scope fence; a
-// reader that observed <memo, done> with a relaxed load performs an acquire
-// fence before reading the data row.
+// reader that observed <memo, done> reads the data row only after an acquire
+// (an acquire load of the bucket, or an acquire fence after a relaxed load).
+// A CAS that returned <memo, done> is followed by the same fence.
 template <int NV>
 __device__ __forceinline__ bool data_equal_after_done(const TableView& t, uint32_t i,
                                                       const Vec<NV>& key, bool acquired) {
@@ -53,7 +72,7 @@ __device__ __forceinline__ bool data_equal_after_done(const TableView& t, uint32
 // Returns false on timeout (error latched).
 __device__ __forceinline__ bool wait_done(const TableView& t, uint32_t i, uint32_t& b,
                                           LocalCounters& lc) {
-  uint32_t spins = 0, ns = 32;
+  uint32_t spins = 0, ns = 16;
   lc.busy_waits++;
   while (!(b & kDone)) {
     if (++spins > t.max_spin) {
@@ -61,7 +80,7 @@ __device__ __forceinline__ bool wait_done(const TableView& t, uint32_t i, uint32
       return false;
     }
     __nanosleep(ns);
-    ns = ns < 2048 ? ns * 2 : ns;
+    ns = ns < 256 ? ns * 2 : ns;
     b = ld_acquire(t.buckets + i);
   }
   return true;
@@ -95,16 +114,16 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
       uint32_t w[8];
       if (v == 0 || v == NS) {
         if (v == 0) {
-          const uint4 a = ld_relaxed_v4(t.buckets + base);
-          const uint4 b = ld_relaxed_v4(t.buckets + base + 4);
+          const uint4 a = ld_bucket_v4(t.buckets + base);
+          const uint4 b = ld_bucket_v4(t.buckets + base + 4);
           first[0] = a.x; first[1] = a.y; first[2] = a.z; first[3] = a.w;
           first[4] = b.x; first[5] = b.y; first[6] = b.z; first[7] = b.w;
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) w[k] = first[k];
       } else {
-        const uint4 a = ld_relaxed_v4(t.buckets + base);
-        const uint4 b = ld_relaxed_v4(t.buckets + base + 4);
+        const uint4 a = ld_bucket_v4(t.buckets + base);
+        const uint4 b = ld_bucket_v4(t.buckets + base + 4);
         w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
         w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
       }
@@ -122,7 +141,7 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
         uint32_t b = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) b = (k == pos) ? w[k] : b;
-        bool acquired = false;
+        bool acquired = (VSS_ACQ_MODE == 1);  // sector words came from acquire loads
         if (b == 0u) {
           const uint32_t old = atomicCAS(t.buckets + i, 0u, memo);  // <memo, write>
           if (old == 0u) {
@@ -135,6 +154,7 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
             return FOP_NEW;
           }
           b = old;
+          acquired = false;  // a relaxed CAS result: fence before reading the row
 #pragma unroll
           for (int k = 0; k < 8; ++k) w[k] = (k == pos) ? old : w[k];
         }
