@@ -44,7 +44,8 @@ enum {
   HT_ERR_FULL = 3,    /* a key found no empty bucket within max_rehash lines */
   HT_ERR_TIMEOUT = 4, /* a bounded wait (write-busy bucket, level barrier) ran out */
   HT_ERR_CUDA = 5,    /* a CUDA runtime call failed */
-  HT_ERR_LEVELS = 6   /* more BFS levels than the caller's level_sizes capacity */
+  HT_ERR_LEVELS = 6,  /* more BFS levels than the caller's level_sizes capacity */
+  HT_ERR_TOO_BIG = 7  /* the request needs more than reach_noalloc's fixed scratch array */
 };
 
 /* Bucket word layout (Section 3.2, "hash memoization" and the write bit):
@@ -227,6 +228,27 @@ ht_status reach_ctx_table(reach_ctx_t* c, ht_t** table);
 /* One-shot reach(model, init): load + run + result on `ctx`. */
 ht_status reach(reach_ctx_t* c, const reach_model* m, const int32_t* init_host, int mode,
                 void* stream, uint64_t* level_sizes_host, uint32_t max_levels, reach_result* out);
+
+/* reach(model, init) for callers that cannot allocate device memory -- code
+ * that must not call cudaMalloc (and so cannot create a context), e.g. a
+ * process whose device memory is fixed at start-up.  There is no counterpart
+ * in the paper; it is the persistent driver run out of one static device
+ * array of 32 MiB (table, both frontiers, counters and level records) that
+ * the library holds on every GPU that loads it, until the process exits.
+ *   - Size limit: reach_ctx_bytes(log2_buckets, state_words, max_levels) must
+ *     not exceed 32 MiB (e.g. 2^18 buckets for W <= 8, 2^17 for W <= 16);
+ *     larger requests return HT_ERR_TOO_BIG and enqueue nothing.
+ *   - Allocates nothing: no cudaMalloc/cudaFree, no pinned host buffers, no
+ *     events.  The array's device address is looked up once per device
+ *     (cudaGetSymbolAddress) by the first call made with that device current;
+ *     make that first call before any stream capture.
+ *   - Every call reuses the same array and clears what must start at zero.
+ *     Calls that overlap on the GPU (other streams, other host threads) race
+ *     on it: serialise them.
+ *   - Synchronous: waits on `stream`, then returns the result like reach(). */
+ht_status reach_noalloc(const reach_model* m, const int32_t* init_host, int log2_buckets,
+                        const ht_params* params, void* stream, uint64_t* level_sizes_host,
+                        uint32_t max_levels, reach_result* out);
 
 /* ------------------------------------------------------------------------ */
 /* Measurement.                                                              */

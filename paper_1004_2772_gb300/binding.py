@@ -20,17 +20,18 @@ import numpy as np
 
 from . import _build
 
-HT_OK, HT_ERR_INVALID, HT_ERR_OOM, HT_ERR_FULL, HT_ERR_TIMEOUT, HT_ERR_CUDA, HT_ERR_LEVELS = range(7)
+(HT_OK, HT_ERR_INVALID, HT_ERR_OOM, HT_ERR_FULL, HT_ERR_TIMEOUT, HT_ERR_CUDA, HT_ERR_LEVELS,
+ HT_ERR_TOO_BIG) = range(8)
 REACH_PERSISTENT, REACH_PER_LEVEL = 0, 1
 STATUS_NAMES = {0: "HT_OK", 1: "HT_ERR_INVALID", 2: "HT_ERR_OOM", 3: "HT_ERR_FULL",
-                4: "HT_ERR_TIMEOUT", 5: "HT_ERR_CUDA", 6: "HT_ERR_LEVELS"}
+                4: "HT_ERR_TIMEOUT", 5: "HT_ERR_CUDA", 6: "HT_ERR_LEVELS", 7: "HT_ERR_TOO_BIG"}
 
 EXPORTED = [
     "ht_bytes", "ht_create", "ht_create_at", "ht_destroy", "ht_clear", "ht_find_or_put", "ht_sync",
     "ht_stats", "ht_scan", "ht_gather", "ht_arrays", "ht_status_string",
     "reach_ctx_bytes", "reach_ctx_create", "reach_ctx_create_at", "reach_ctx_destroy",
     "reach_ctx_load", "reach_ctx_run", "reach_ctx_result", "reach_ctx_table", "reach",
-    "reach_ctx_last_timing", "reach_ctx_level_ns", "vss_probe_random",
+    "reach_ctx_last_timing", "reach_ctx_level_ns", "vss_probe_random", "reach_noalloc",
 ]
 
 
@@ -115,6 +116,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "reach_ctx_last_timing": [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint32)],
         "reach_ctx_level_ns": [_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)],
         "vss_probe_random": [_VP, _u64, _u64, _i, _VP, ctypes.POINTER(ctypes.c_float)],
+        "reach_noalloc": [ctypes.POINTER(reach_model), _VP, _i, ctypes.POINTER(ht_params), _VP, _VP,
+                          ctypes.c_uint32, ctypes.POINTER(reach_result)],
         "reach": [_VP, ctypes.POINTER(reach_model), _VP, _i, _VP, _VP, ctypes.c_uint32,
                   ctypes.POINTER(reach_result)],
     }
@@ -302,6 +305,19 @@ def random_access_rates(gib: int = 16, n_access: int = 1 << 28, device="cuda") -
         out[mode] = n_access / (ms / 1e3)
     del buf
     return out
+
+
+def reach_noalloc(model, log2_buckets: int, params: ht_params | None = None, stream: int = 0,
+                  max_levels: int = 4096):
+    """reach() without device allocation (fixed 32 MiB scratch array inside the
+    library); returns (status, reach_result, level sizes)."""
+    a = _ModelArgs(model)
+    levels = np.zeros(max_levels, dtype=np.uint64)
+    r = reach_result()
+    st = load().reach_noalloc(ctypes.byref(a.struct), a.init.ctypes.data, log2_buckets,
+                              ctypes.byref(params) if params else None, stream, levels.ctypes.data,
+                              max_levels, ctypes.byref(r))
+    return st, r, levels[:min(r.n_levels, max_levels)].astype(np.int64)
 
 
 # ---------------------------------------------------------------------------

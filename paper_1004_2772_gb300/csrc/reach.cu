@@ -16,6 +16,7 @@
 //   per-level   one launch per level; the host reads the next level's size.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -814,3 +815,144 @@ ht_status reach(reach_ctx_t* c, const reach_model* m, const int32_t* init_host, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// reach_noalloc: reachability that allocates no device memory.
+//
+// For callers that cannot call cudaMalloc (a host process that must not grow
+// its device footprint after start-up, code running where allocation is not
+// allowed).  The table, the two frontiers and the counters live in one
+// file-scope device array of kNoAllocScratchBytes, loaded with the library and
+// held by every GPU that loads it until the process exits.  Host code cannot
+// use the array's name as a device address; its address is obtained once per
+// device with cudaGetSymbolAddress, on the first call made with that device
+// current.
+// ---------------------------------------------------------------------------
+namespace vss {
+
+constexpr uint64_t kNoAllocScratchBytes = 32ull << 20;
+constexpr int kNoAllocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+static ht_status noalloc_scratch(void** out) {
+  int dev = 0;
+  VSS_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return HT_ERR_INVALID;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      cudaGetLastError();
+      return HT_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return HT_OK;
+}
+
+}  // namespace vss
+
+extern "C" ht_status reach_noalloc(const reach_model* m, const int32_t* init_host, int log2_buckets,
+                                   const ht_params* params, void* stream,
+                                   uint64_t* level_sizes_host, uint32_t max_levels,
+                                   reach_result* out) {
+  if (!m || !init_host || !out || max_levels < 1) return HT_ERR_INVALID;
+  std::memset(out, 0, sizeof(*out));
+  const int W = m->state_words;
+  uint64_t need = 0;
+  ht_status st = reach_ctx_bytes(log2_buckets, W, max_levels, &need);
+  if (st != HT_OK) return st;
+  if (need > kNoAllocScratchBytes) return HT_ERR_TOO_BIG;
+  void* base = nullptr;
+  st = noalloc_scratch(&base);
+  if (st != HT_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // carve the scratch array exactly like a context block
+  ht_t table;
+  const uint64_t tb = align_up(table_bytes(log2_buckets, W), 256);
+  st = table_init_at(&table, log2_buckets, W, params, base, tb);
+  if (st != HT_OK) return st;
+  char* p = static_cast<char*>(base) + tb;
+  int* blob = reinterpret_cast<int*>(p);
+  p += align_up(kModelMaxWords * 4ull, 256);
+  const uint64_t fb = frontier_bytes(log2_buckets, W);
+  uint4* f0 = reinterpret_cast<uint4*>(p);
+  p += fb;
+  uint4* f1 = reinterpret_cast<uint4*>(p);
+  p += fb;
+  ReachTotals* tot = reinterpret_cast<ReachTotals*>(p);
+  p += align_up(sizeof(ReachTotals), 256);
+  unsigned long long* lsz = reinterpret_cast<unsigned long long*>(p);
+  p += align_up((uint64_t)max_levels * 8, 256);
+  unsigned long long* lns = reinterpret_cast<unsigned long long*>(p);
+
+  std::vector<int> host_blob;
+  st = pack_model(m, init_host, W, host_blob);
+  if (st != HT_OK) return st;
+  const int threads = (int)table.params.block_threads;
+  const int smem_words = host_blob[11];
+  const size_t smem = (size_t)((smem_words + 3) & ~3) * 4 +
+                      (size_t)(threads / 32) * warp_smem_words_nv((int)table.view.nv) * 4;
+  if (smem > 200 * 1024) return HT_ERR_INVALID;
+  int dev = 0, coop = 0;
+  VSS_CUDA_TRY(cudaGetDevice(&dev));
+  VSS_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return HT_ERR_CUDA;
+
+  // everything that must start at zero is cleared: the previous call's table,
+  // frontier counts, cursors and barrier words are still in the array
+  VSS_CUDA_TRY(cudaMemcpyAsync(blob, host_blob.data(), host_blob.size() * 4,
+                               cudaMemcpyHostToDevice, s));
+  st = table_clear(&table, s);
+  if (st != HT_OK) return st;
+  VSS_CUDA_TRY(cudaMemsetAsync(tot, 0, sizeof(ReachTotals), s));
+
+  const ReachKernels ks = pick_kernels((int)table.view.nv, (int)table.params.line_buckets);
+  VSS_CUDA_TRY(cudaFuncSetAttribute(ks.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int per_sm = 0;
+  VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.persistent, threads, smem));
+  if (per_sm < 1) return HT_ERR_INVALID;
+  TableView tv = table.view;
+  ReachDev rd;
+  rd.blob = blob;
+  rd.smem_words = smem_words;
+  rd.frontier0 = f0;
+  rd.frontier1 = f1;
+  rd.cap = (uint32_t)(1ull << log2_buckets);
+  rd.tot = tot;
+  rd.level_sizes = lsz;
+  rd.level_ns = lns;
+  rd.max_levels = max_levels;
+  rd.bar_spin = 1u << 22;
+  void* args[] = {&tv, &rd};
+  VSS_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(ks.persistent),
+                                           per_sm * table.num_sms, threads, args, smem, s));
+
+  ReachTotals t;
+  DevCounters ctr;
+  VSS_CUDA_TRY(cudaMemcpyAsync(&t, tot, sizeof(t), cudaMemcpyDeviceToHost, s));
+  VSS_CUDA_TRY(cudaMemcpyAsync(&ctr, table.view.ctr, sizeof(ctr), cudaMemcpyDeviceToHost, s));
+  VSS_CUDA_TRY(cudaStreamSynchronize(s));
+  out->states = ctr.stored;
+  out->transitions = t.transitions;
+  out->deadlocks = t.deadlocks;
+  out->digest = t.digest;
+  out->busy_waits = ctr.busy_waits;
+  out->rehashes = ctr.rehashes;
+  out->n_levels = t.n_levels;
+  out->status = (ht_status)ctr.err;
+  if (level_sizes_host && out->n_levels) {
+    const uint32_t n = std::min(out->n_levels, max_levels);
+    VSS_CUDA_TRY(cudaMemcpyAsync(level_sizes_host, lsz, (size_t)n * 8, cudaMemcpyDeviceToHost, s));
+    VSS_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return out->status;
+}

@@ -256,6 +256,7 @@ const char* ht_status_string(ht_status s) {
     case HT_ERR_TIMEOUT: return "bounded wait ran out";
     case HT_ERR_CUDA: return "CUDA runtime error";
     case HT_ERR_LEVELS: return "more BFS levels than the level_sizes capacity";
+    case HT_ERR_TOO_BIG: return "request exceeds the fixed scratch array of reach_noalloc";
     default: return "unknown status";
   }
 }
