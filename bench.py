@@ -35,7 +35,7 @@ from paper_1004_2772_gb300 import synth  # noqa: E402
 METRIC = "states/sec & find_or_put ops/sec on 1 GB300; fraction of HBM random-sector roofline"
 # BEEM-shaped: 12 guarded processes, 4 shared vars in [0,4), mutex, W = 16
 WORKLOADS = {
-    "beem": (dict(seed=7, update_pct=40), 26),
+    "beem": (dict(seed=22, update_pct=40), 26),
     "beem-medium": (dict(seed=7, update_pct=40), 24),
     "tiny": (None, 18),
 }
@@ -129,6 +129,26 @@ def algorithmic_bytes(states, transitions, state_words=16):
     new = states - 1
     dup = transitions - new
     return states * (row + 4) + dup * (32 + row) + new * (64 + row + 4)
+
+
+def random_roofline(states, transitions, kernel_ms, rates, hbm_gbs, state_words=16):
+    """Time the run would take if every random access ran at the probe-measured
+    random-access rate of this GPU (`vss_probe_random`) and the frontier rows
+    streamed at copy bandwidth:
+      per transition        one random 32 B bucket-sector read
+      per duplicate         one random 64 B row read (the compare)
+      per new state         three random 32 B sector writes (row + bucket write-back)
+      per expanded state    its frontier row read and, once, written (streamed)."""
+    row = 16 * ((state_words + 3) // 4)
+    new = states - 1
+    dup = transitions - new
+    t = (transitions / rates[0] + dup / rates[1] + 3 * new / rates[2]
+         + 2 * states * row / (hbm_gbs * 1e9))
+    return {"bound_ms": t * 1e3, "kernel_ms": kernel_ms, "frac": (t * 1e3) / kernel_ms,
+            "find_or_put_bound_per_s": transitions / t,
+            "probe_rates_per_s": {"read32": rates[0], "read64": rates[1], "write32": rates[2],
+                                  "atomic32": rates[3]},
+            "unit": "fraction of the random-access bound (probe-measured rates)"}
 
 
 def dist_setup():
@@ -234,6 +254,8 @@ def main():
     _build.build()
     binding.load()
 
+    # random-access rates of this GPU (the random-sector roofline's denominators)
+    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
     model = workload_model(args.workload)
     mode = binding.REACH_PERSISTENT if args.mode == "persistent" else binding.REACH_PER_LEVEL
     ctx = binding.ReachContext(LOG2_BUCKETS, model.state_words, max_levels=MAX_LEVELS,
@@ -309,6 +331,8 @@ def main():
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_reach_persistent" if mode == 0 else "k_reach_level",
                      "kernel_ms": kernel_ms, "algorithmic_bytes": alg, "peak_source": which},
+        "random_roofline": random_roofline(got.states, got.transitions, kernel_ms, rates, peak,
+                                           model.state_words),
         "e2e": {"value": states_all / (e2e_ms / 1000.0), "unit": "states/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
         "gpu_launches": launches * args.steps,

@@ -136,6 +136,33 @@ ht_status ht_gather(ht_t* h, const uint32_t* idx_dev, uint64_t n, int32_t* out_d
 ht_status ht_arrays(ht_t* h, uint32_t** buckets_dev, int32_t** data_dev, uint32_t* row_words);
 
 /* ------------------------------------------------------------------------ */
+/* Hash-table benchmark streams (Section 4.3 measures find-or-put throughput  */
+/* on synthetic keys; these generate such keys on the device).               */
+/* ------------------------------------------------------------------------ */
+
+/* A fill with n_ids distinct keys is a stream of 2*n_ids calls: call 2i is key
+ * i; call 2i+1 repeats a key drawn from r = mix(c ^ mix(seed)) -- uniformly
+ * from ids [0, i] when zipf_table_dev is NULL, else from ranks 1..n_ids of a
+ * Zipf quantile table (65537 uint32 entries: a cell from the top 16 bits of r,
+ * a rank uniform inside the cell).  Key i: word 0 = MurmurHash3 fmix32(i),
+ * word j >= 1 = low 32 bits of mix((seed << 36) + (i << 4) + j), mix = one
+ * SplitMix64 output step.
+ * vss_gen_keys writes calls [call_begin, call_begin + n_calls) as rows of
+ * state_words int32 to keys_dev.  Enqueued on stream. */
+ht_status vss_gen_keys(uint64_t seed, uint64_t n_ids, uint64_t call_begin, uint64_t n_calls,
+                       const uint32_t* zipf_table_dev, int state_words, int32_t* keys_dev,
+                       void* stream);
+
+/* find-or-put of calls [call_begin, call_begin + n_calls) of that stream, the
+ * keys generated in registers (no key traffic).  result_dev (2 uint64, the
+ * caller zeroes them) accumulates the number of keys this call stored and the
+ * sum of their fingerprints (the digest of ht_scan).  Needs state_words with
+ * ceil(state_words/4) in {1, 2, 4, 8}.  Enqueued on stream. */
+ht_status ht_find_or_put_stream(ht_t* h, uint64_t seed, uint64_t n_ids, uint64_t call_begin,
+                                uint64_t n_calls, const uint32_t* zipf_table_dev,
+                                uint64_t* result_dev, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Reachability (Alg. "Reachability analysis", level-synchronous BFS).        */
 /* ------------------------------------------------------------------------ */
 

@@ -32,6 +32,7 @@ EXPORTED = [
     "reach_ctx_bytes", "reach_ctx_create", "reach_ctx_create_at", "reach_ctx_destroy",
     "reach_ctx_load", "reach_ctx_run", "reach_ctx_result", "reach_ctx_table", "reach",
     "reach_ctx_last_timing", "reach_ctx_level_ns", "vss_probe_random", "reach_noalloc",
+    "vss_gen_keys", "ht_find_or_put_stream",
 ]
 
 
@@ -116,6 +117,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "reach_ctx_last_timing": [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint32)],
         "reach_ctx_level_ns": [_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)],
         "vss_probe_random": [_VP, _u64, _u64, _i, _VP, ctypes.POINTER(ctypes.c_float)],
+        "vss_gen_keys": [_u64, _u64, _u64, _u64, _VP, _i, _VP, _VP],
+        "ht_find_or_put_stream": [_VP, _u64, _u64, _u64, _u64, _VP, _VP, _VP],
         "reach_noalloc": [ctypes.POINTER(reach_model), _VP, _i, ctypes.POINTER(ht_params), _VP, _VP,
                           ctypes.c_uint32, ctypes.POINTER(reach_result)],
         "reach": [_VP, ctypes.POINTER(reach_model), _VP, _i, _VP, _VP, ctypes.c_uint32,
@@ -282,6 +285,15 @@ def reach(c: int, model, mode: int = REACH_PERSISTENT, stream: int = 0, max_leve
     return st, r, levels[:min(r.n_levels, max_levels)].astype(np.int64)
 
 
+def vss_gen_keys(seed, n_ids, call_begin, n_calls, zipf_dev, state_words, keys_dev, stream=0) -> int:
+    return load().vss_gen_keys(seed, n_ids, call_begin, n_calls, zipf_dev, state_words, keys_dev, stream)
+
+
+def ht_find_or_put_stream(h, seed, n_ids, call_begin, n_calls, zipf_dev, result_dev, stream=0) -> int:
+    return load().ht_find_or_put_stream(h, seed, n_ids, call_begin, n_calls, zipf_dev, result_dev,
+                                        stream)
+
+
 def vss_probe_random(buf_dev: int, nbytes: int, n_access: int, mode: int, stream: int = 0) -> float:
     ms = ctypes.c_float()
     _check(load().vss_probe_random(buf_dev, nbytes, n_access, mode, stream, ctypes.byref(ms)),
@@ -379,6 +391,40 @@ class Table:
                               idx.data_ptr() if idx is not None else 0, current_stream()),
                "ht_find_or_put")
         return seen, idx
+
+    def find_or_put_stream(self, seed: int, n_ids: int, call_begin: int, n_calls: int,
+                           zipf_table=None, sync: bool = True):
+        """Fused generator + find-or-put over calls [call_begin, call_begin+n_calls)
+        of the fill with n_ids keys; returns (new keys, digest of the stored keys)."""
+        torch = _torch()
+        zt = self._zipf_dev(zipf_table)
+        res = torch.zeros(2, dtype=torch.int64, device=self.mem.device)
+        _check(ht_find_or_put_stream(self.handle, seed, n_ids, call_begin, n_calls,
+                                     zt.data_ptr() if zt is not None else 0, res.data_ptr(),
+                                     current_stream()), "ht_find_or_put_stream")
+        if not sync:
+            return res
+        v = res.cpu().numpy().view(np.uint64)
+        return int(v[0]), int(v[1])
+
+    def _zipf_dev(self, zipf_table):
+        if zipf_table is None:
+            return None
+        torch = _torch()
+        key = id(zipf_table)
+        if getattr(self, "_zipf_key", None) != key:
+            self._zipf = torch.from_numpy(np.ascontiguousarray(zipf_table, dtype=np.uint32).view(np.int32)).to(self.mem.device)
+            self._zipf_key = key
+        return self._zipf
+
+    def gen_keys(self, seed: int, n_ids: int, call_begin: int, n_calls: int, zipf_table=None):
+        """The keys of calls [call_begin, call_begin+n_calls) as an int32 CUDA tensor."""
+        torch = _torch()
+        zt = self._zipf_dev(zipf_table)
+        out = torch.empty((n_calls, self.state_words), dtype=torch.int32, device=self.mem.device)
+        _check(vss_gen_keys(seed, n_ids, call_begin, n_calls, zt.data_ptr() if zt is not None else 0,
+                            self.state_words, out.data_ptr(), current_stream()), "vss_gen_keys")
+        return out
 
     def sync(self) -> int:
         return ht_sync(self.handle, current_stream())

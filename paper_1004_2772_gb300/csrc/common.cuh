@@ -71,6 +71,28 @@ __device__ __forceinline__ uint4 ld_acquire_v4(const void* p) {
                : "memory");
   return v;
 }
+// 32-byte accesses (one full L2 sector per instruction; the address must be
+// 32-byte aligned).
+#define VSS_V8_OUT(a, b) "=r"(a.x), "=r"(a.y), "=r"(a.z), "=r"(a.w), "=r"(b.x), "=r"(b.y), "=r"(b.z), "=r"(b.w)
+__device__ __forceinline__ void ld_acquire_v8(const void* p, uint4& a, uint4& b) {
+  asm volatile("ld.acquire.gpu.global.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : VSS_V8_OUT(a, b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void ld_relaxed_v8(const void* p, uint4& a, uint4& b) {
+  asm volatile("ld.relaxed.gpu.global.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : VSS_V8_OUT(a, b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void ld_cg_v8(const void* p, uint4& a, uint4& b) {
+  asm volatile("ld.global.cg.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : VSS_V8_OUT(a, b) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void st_v8(void* p, const uint4& a, const uint4& b) {
+  asm volatile("st.global.v8.u32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "r"(a.x), "r"(a.y),
+               "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+               : "memory");
+}
+#undef VSS_V8_OUT
+
 __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -131,16 +153,19 @@ __device__ __forceinline__ bool vec_eq(const Vec<NV>& a, const Vec<NV>& b) {
 }
 
 // ---------------------------------------------------------------------------
-// Table hash.  The paper leaves the hash family open (Section 3.3: h_num);
-// this is a single-lane MurmurHash3-x64 style accumulation (Appleby, public
-// domain MurmurHash3: per 64-bit block k *= c1, k = rotl(k,31), k *= c2,
-// h ^= k, h = rotl(h,27)*5 + 0x52dce729) over the padded vector, finished with
-// the MurmurHash3 fmix64 avalanche.  One hash serves every rehash round: the
-// index comes from its low bits, the memo from bits 33..63, the double-hashing
-// step from the memo.
+// Table hash.  The paper leaves the hash family open (Section 3.3: h_num).
+// This one is a position-keyed additive hash finished by the MurmurHash3
+// fmix64 avalanche (Appleby, public domain):
+//   S(v)  = sum over words k < W of term(k, v_k)          (mod 2^64)
+//   term  = z ^ (z >> 29),  z = (v_k xor c_k) * 0xBF58476D1CE4E5B9,
+//           c_k = seed + (k + 1) * 0x9E3779B97F4A7C15
+//   h(v)  = fmix64(S(v) + W)
+// term(k, .) is injective, so vectors differing in one word never collide in
+// S, and a successor that changes words p and q of its parent v gets
+// S = S(v) - term(p, v_p) + term(p, x) [- term(q, v_q) + term(q, y)] in a few
+// instructions.  One hash serves every rehash round: the index comes from its
+// low bits, the memo from bits 33..63, the double-hashing step from the memo.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint64_t rotl64(uint64_t x, int r) { return (x << r) | (x >> (64 - r)); }
-
 __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
   k ^= k >> 33;
   k *= 0xff51afd7ed558ccdULL;
@@ -150,25 +175,26 @@ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
   return k;
 }
 
-__device__ __forceinline__ uint64_t murmur_block(uint64_t h, uint64_t k) {
-  k *= 0x87c37b91114253d5ULL;
-  k = rotl64(k, 31);
-  k *= 0x4cf5ad432745937fULL;
-  h ^= k;
-  h = rotl64(h, 27);
-  return h * 5 + 0x52dce729ULL;
+__device__ __forceinline__ uint64_t hash_term(uint64_t seed, int k, uint32_t x) {
+  const uint64_t z = ((uint64_t)x ^ (seed + (uint64_t)(k + 1) * 0x9E3779B97F4A7C15ULL)) *
+                     0xBF58476D1CE4E5B9ULL;
+  return z ^ (z >> 29);
 }
 
 template <int NV>
-__device__ __forceinline__ uint64_t table_hash(const Vec<NV>& v, uint32_t W, uint64_t seed) {
-  uint64_t h = seed;
+__device__ __forceinline__ uint64_t hash_sum(const Vec<NV>& v, uint32_t W, uint64_t seed) {
+  uint64_t s = 0;
 #pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    h = murmur_block(h, (uint64_t)v.c[j].x | ((uint64_t)v.c[j].y << 32));
-    h = murmur_block(h, (uint64_t)v.c[j].z | ((uint64_t)v.c[j].w << 32));
-  }
-  h ^= (uint64_t)W * 4u;
-  return fmix64(h);
+  for (int k = 0; k < 4 * NV; ++k)
+    if (k < (int)W) s += hash_term(seed, k, vec_word(v, k));
+  return s;
+}
+
+__device__ __forceinline__ uint64_t hash_final(uint64_t s, uint32_t W) { return fmix64(s + W); }
+
+template <int NV>
+__device__ __forceinline__ uint64_t table_hash(const Vec<NV>& v, uint32_t W, uint64_t seed) {
+  return hash_final(hash_sum(v, W, seed), W);
 }
 
 __device__ __forceinline__ uint32_t memo_of(uint64_t h) {
@@ -197,11 +223,41 @@ __device__ __forceinline__ uint64_t fingerprint(const Vec<NV>& v, uint32_t W) {
   return x;
 }
 
+// Rows of an even number of 16-byte chunks are 32-byte aligned: move them a
+// sector per instruction.
 // Load a data row (nv chunks) with strong gpu-scope loads.
 template <int NV>
 __device__ __forceinline__ void load_row(const uint4* row, Vec<NV>& v) {
+  if (NV % 2 == 0) {
 #pragma unroll
-  for (int j = 0; j < NV; ++j) v.c[j] = ld_relaxed_v4(row + j);
+    for (int j = 0; j < NV; j += 2) ld_relaxed_v8(row + j, v.c[j], v.c[(j + 1) % NV]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v.c[j] = ld_relaxed_v4(row + j);
+  }
+}
+
+// Load a frontier row (written before the last grid barrier) through L2.
+template <int NV>
+__device__ __forceinline__ void load_row_cg(const uint4* row, Vec<NV>& v) {
+  if (NV % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; j += 2) ld_cg_v8(row + j, v.c[j], v.c[(j + 1) % NV]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v.c[j] = __ldcg(row + j);
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void store_row(uint4* row, const Vec<NV>& v) {
+  if (NV % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; j += 2) st_v8(row + j, v.c[j], v.c[(j + 1) % NV]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) row[j] = v.c[j];
+  }
 }
 
 }  // namespace vss

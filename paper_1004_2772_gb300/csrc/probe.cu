@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256) k_probe(uint4* buf, uint64_t n_units, uin
       for (int k = 0; k < kInflight; ++k) {
         const uint4* p = buf + u[k] * (MODE == 1 ? 4 : 2);
 #pragma unroll
-        for (int q = 0; q < (MODE == 1 ? 4 : 2); ++q) v[k][q] = __ldcg(p + q);
+        for (int q = 0; q < (MODE == 1 ? 4 : 2); q += 2) ld_cg_v8(p + q, v[k][q], v[k][q + 1]);
       }
 #pragma unroll
       for (int k = 0; k < kInflight; ++k)
@@ -48,10 +48,8 @@ __global__ void __launch_bounds__(256) k_probe(uint4* buf, uint64_t n_units, uin
 #pragma unroll
       for (int k = 0; k < kInflight; ++k) {
         if (base + k < n_access) {
-          uint4* p = buf + u[k] * 2;
           const uint4 w = make_uint4((uint32_t)u[k], (uint32_t)k, 0u, 0u);
-          __stcg(p, w);
-          __stcg(p + 1, w);
+          st_v8(buf + u[k] * 2, w, w);
         }
       }
     } else {

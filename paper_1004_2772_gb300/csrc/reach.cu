@@ -27,7 +27,7 @@ namespace vss {
 
 constexpr int kDescCap = 1024;
 #ifndef VSS_REACH_MINB
-#define VSS_REACH_MINB 1  // __launch_bounds__ minimum resident blocks of the expansion kernels
+#define VSS_REACH_MINB 3  // __launch_bounds__ minimum resident blocks of the expansion kernels
 #endif             // successor descriptors per warp and round
 constexpr int kModelMaxWords = 1 << 15;    // model blob capacity (int32 words, 128 KiB)
 constexpr int kHdr = 16;                   // blob header words
@@ -60,8 +60,8 @@ struct __align__(16) ReachTotals {
   unsigned long long stored;
   uint32_t counts[4];   // frontier sizes, rotating over 3 levels
   uint32_t cursor[4];   // next unclaimed frontier row of a level, rotating over 3 levels
-  uint32_t bar_count;
-  uint32_t bar_gen;
+  uint32_t bar_count;   // grid-barrier arrivals since the run started (only grows)
+  uint32_t bar_pad;
   uint32_t n_levels;
   uint32_t pad;
 };
@@ -145,19 +145,36 @@ __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, c
   spw = spw < 1u ? 1u : (spw > (uint32_t)m.spw_max ? (uint32_t)m.spw_max : spw);
   const int P = m.P;
   const int maxfan = m.maxfan;
-  for (;;) {
-    // rounds are claimed dynamically, so warps that finish early take more
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(cursor, spw);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    if (base >= n_cur) break;
+  const uint32_t warp_id = blockIdx.x * wpb + (threadIdx.x >> 5);
+  const uint64_t static_rows = (uint64_t)warps * spw;
+  for (bool first = true;; first = false) {
+    // the first round is static (warp w takes rows w*spw ..); later rounds are
+    // claimed from the level cursor, so warps that finish early take more,
+    // and a level that fits in one round costs no atomic at all
+    uint64_t base = (uint64_t)warp_id * spw;
+    if (!first) {
+      if (static_rows >= n_cur) break;
+      uint32_t c0 = 0;
+      if (lane == 0) c0 = atomicAdd(cursor, spw);
+      base = static_rows + __shfl_sync(0xffffffffu, c0, 0);
+    }
+    if (base >= n_cur) {
+      if (first) continue;
+      break;
+    }
     // ---- phase 1: expand the round's states into successor descriptors
     uint32_t c = 0;
-    const uint64_t f = (uint64_t)base + lane;
+    const uint64_t f = base + lane;
     if (lane < spw && f < n_cur) {
       uint4* r = reinterpret_cast<uint4*>(rows + lane * RS);
+      Vec<NV> v;
+      load_row_cg<NV>(cur + f * NV, v);
 #pragma unroll
-      for (int j = 0; j < NV; ++j) r[j] = __ldcg(cur + f * NV + j);
+      for (int j = 0; j < NV; ++j) r[j] = v.c[j];
+      // the parent's hash sum, kept in the row's padding for its successors
+      const uint64_t hs = hash_sum(v, t.state_words, t.seed);
+      rows[lane * RS + 4 * NV] = (uint32_t)hs;
+      rows[lane * RS + 4 * NV + 1] = (uint32_t)(hs >> 32);
       const int* rw = reinterpret_cast<const int*>(rows + lane * RS);
       int ncrit = 0;
       if (m.crit_any) {
@@ -210,12 +227,21 @@ __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, c
         const int e = (int)(dd & 0xFFFFFFu);
         const int p = (int)(dd >> 24);
         const int4 E = m.edges[e];
-        const uint4* r = reinterpret_cast<const uint4*>(rows + o * RS);
+        const uint32_t* ro = rows + o * RS;
+        const uint4* r = reinterpret_cast<const uint4*>(ro);
 #pragma unroll
         for (int q = 0; q < NV; ++q) w.c[q] = r[q];
+        // successor hash from the parent's sum: only words p (and P + upd_var) change
+        uint64_t hs = (uint64_t)ro[4 * NV] | ((uint64_t)ro[4 * NV + 1] << 32);
+        hs += hash_term(t.seed, p, (uint32_t)E.x) - hash_term(t.seed, p, ro[p]);
         vec_set(w, p, (uint32_t)E.x);
-        if (E.w >= 0) vec_set(w, P + E.w, (uint32_t)m.uval[e]);
-        const uint64_t h = table_hash(w, t.state_words, t.seed);
+        if (E.w >= 0) {
+          const int q = P + E.w;
+          const uint32_t uv = (uint32_t)m.uval[e];
+          hs += hash_term(t.seed, q, uv) - hash_term(t.seed, q, ro[q]);
+          vec_set(w, q, uv);
+        }
+        const uint64_t h = hash_final(hs, t.state_words);
         uint32_t sidx = 0;
         const int res = find_or_put<NV, L>(t, w, h, sidx, lc);
         if (res == FOP_NEW) {
@@ -232,9 +258,7 @@ __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, c
         if (is_new) {
           const uint32_t pos = wbase + __popc(nb & ((1u << lane) - 1u));
           if (pos < cap) {
-            uint4* dst = next + (size_t)pos * NV;
-#pragma unroll
-            for (int q = 0; q < NV; ++q) dst[q] = w.c[q];
+            store_row<NV>(next + (size_t)pos * NV, w);
           } else {
             latch_error(t.ctr, HT_ERR_FULL);
           }
@@ -292,28 +316,26 @@ __device__ void seed_init(const TableView& t, const ReachDev& rd, Acc& acc, Loca
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// wait is bounded: after `limit` polls the barrier latches HT_ERR_TIMEOUT and
-// returns false; it also returns false as soon as any error is latched, so
-// every block leaves the kernel instead of waiting for one that already left.
-__device__ bool grid_barrier(const ReachDev& rd, DevCounters* ctr) {
+// arrival counter only grows: barrier number e completes when it reaches
+// e * gridDim.x, so arriving is one release-add and waiting one acquire poll
+// (no reset, no second flag).  The wait is bounded: after `bar_spin` polls the
+// barrier latches HT_ERR_TIMEOUT and returns false; it also returns false as
+// soon as any error is latched, so every block leaves the kernel instead of
+// waiting for one that already left.
+__device__ bool grid_barrier(const ReachDev& rd, DevCounters* ctr, uint32_t& epoch) {
   __shared__ int ok;
   __syncthreads();
+  ++epoch;
   if (threadIdx.x == 0) {
     int good = 1;
-    const uint32_t gen = ld_acquire(&rd.tot->bar_gen);
-    fence_acq_rel();
-    const uint32_t arrived = atomicAdd(&rd.tot->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
-      st_relaxed(&rd.tot->bar_count, 0u);
-      st_release(&rd.tot->bar_gen, gen + 1);
-    } else {
-      uint32_t spins = 0, ns = 32;
-      while (ld_acquire(&rd.tot->bar_gen) == gen) {
-        if (ld_relaxed(&ctr->err) != 0) { good = 0; break; }
-        if (++spins > rd.bar_spin) { latch_error(ctr, HT_ERR_TIMEOUT); good = 0; break; }
-        __nanosleep(ns);
-        ns = ns < 256 ? ns * 2 : ns;
-      }
+    const uint32_t target = epoch * gridDim.x;
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&rd.tot->bar_count) : "memory");
+    uint32_t spins = 0, ns = 32;
+    while (ld_acquire(&rd.tot->bar_count) < target) {
+      if (ld_relaxed(&ctr->err) != 0) { good = 0; break; }
+      if (++spins > rd.bar_spin) { latch_error(ctr, HT_ERR_TIMEOUT); good = 0; break; }
+      __nanosleep(ns);
+      ns = ns < 256 ? ns * 2 : ns;
     }
     if (ld_relaxed(&ctr->err) != 0) good = 0;
     ok = good;
@@ -334,7 +356,8 @@ __global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_persistent(TableV
     seed_init<NV, L>(t, rd, acc, lc);
     rd.level_ns[0] = global_ns();
   }
-  if (grid_barrier(rd, t.ctr)) {
+  uint32_t epoch = 0;
+  if (grid_barrier(rd, t.ctr, epoch)) {
     uint32_t k = 0;
     for (;;) {
       const uint32_t n_cur = ld_relaxed(&rd.tot->counts[k % 3]);
@@ -346,7 +369,7 @@ __global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_persistent(TableV
         st_relaxed(&rd.tot->counts[(k + 2) % 3], 0u);
         st_relaxed(&rd.tot->cursor[(k + 2) % 3], 0u);
       }
-      if (!grid_barrier(rd, t.ctr)) break;
+      if (!grid_barrier(rd, t.ctr, epoch)) break;
       const uint32_t n_next = ld_relaxed(&rd.tot->counts[(k + 1) % 3]);
       if (n_next == 0) break;
       ++k;

@@ -40,11 +40,12 @@ namespace vss {
 #define VSS_ACQ_MODE 1
 #endif
 
-__device__ __forceinline__ uint4 ld_bucket_v4(const uint32_t* p) {
+// One 32-byte bucket sector in one instruction.
+__device__ __forceinline__ void ld_sector(const uint32_t* p, uint4& a, uint4& b) {
 #if VSS_ACQ_MODE == 1
-  return ld_acquire_v4(p);
+  ld_acquire_v8(p, a, b);
 #else
-  return ld_relaxed_v4(p);
+  ld_relaxed_v8(p, a, b);
 #endif
 }
 
@@ -114,16 +115,16 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
       uint32_t w[8];
       if (v == 0 || v == NS) {
         if (v == 0) {
-          const uint4 a = ld_bucket_v4(t.buckets + base);
-          const uint4 b = ld_bucket_v4(t.buckets + base + 4);
+          uint4 a, b;
+          ld_sector(t.buckets + base, a, b);
           first[0] = a.x; first[1] = a.y; first[2] = a.z; first[3] = a.w;
           first[4] = b.x; first[5] = b.y; first[6] = b.z; first[7] = b.w;
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) w[k] = first[k];
       } else {
-        const uint4 a = ld_bucket_v4(t.buckets + base);
-        const uint4 b = ld_bucket_v4(t.buckets + base + 4);
+        uint4 a, b;
+        ld_sector(t.buckets + base, a, b);
         w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
         w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
       }
@@ -145,9 +146,7 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
         if (b == 0u) {
           const uint32_t old = atomicCAS(t.buckets + i, 0u, memo);  // <memo, write>
           if (old == 0u) {
-            uint4* row = t.data + (size_t)i * NV;
-#pragma unroll
-            for (int j = 0; j < NV; ++j) row[j] = key.c[j];
+            store_row<NV>(t.data + (size_t)i * NV, key);
             fence_acq_rel();                 // data before <memo, done>
             st_relaxed(t.buckets + i, memo | kDone);
             out_idx = i;

@@ -20,8 +20,8 @@ from paper_1004_2772_gb300 import synth  # noqa: E402
 CASES = {
     # 12 guarded processes, 4 shared variables, mutex; 5.5M states
     "beem_medium": dict(model=dict(seed=7, update_pct=40), log2_buckets=24),
-    # the BEEM-shaped workload: 12 processes, 4 shared variables in [0,4), W = 16
-    "beem_c2": dict(model=dict(seed=7, update_pct=40), log2_buckets=26),
+    # the BEEM-shaped workload: 12 processes, 4 shared variables in [0,4), W = 16; 32M states
+    "beem_c2": dict(model=dict(seed=22, update_pct=40), log2_buckets=26),
 }
 
 

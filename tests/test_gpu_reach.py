@@ -138,3 +138,17 @@ def test_beem_shaped_medium(cuda_lib):
         assert (got.states, got.transitions, got.deadlocks, got.digest) == (
             g["states"], g["transitions"], g["deadlocks"], int(g["digest"], 16))
         assert got.level_sizes == g["level_sizes"]
+
+
+def test_beem_shaped_workload_full_size(cuda_lib):
+    """The benchmarked BEEM-shaped workload (32M states, 2^26 buckets), in the
+    launch configuration bench.py times, against the oracle's stored result."""
+    g = load_golden("beem_c2.json")
+    m = synth.beem_shaped_model(**g["model"])
+    ctx = cuda_lib.ReachContext(g["log2_buckets"], 16, max_levels=1 << 14)
+    got = ctx.reach(m, mode=0)
+    assert (got.states, got.transitions, got.deadlocks, got.digest) == (
+        g["states"], g["transitions"], g["deadlocks"], int(g["digest"], 16))
+    assert got.level_sizes == g["level_sizes"]
+    done, writing, digest = ctx.scan()
+    assert (done, writing, digest) == (g["states"], 0, int(g["digest"], 16))
