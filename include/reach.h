@@ -256,6 +256,59 @@ ht_status reach_ctx_table(reach_ctx_t* c, ht_t** table);
 ht_status reach(reach_ctx_t* c, const reach_model* m, const int32_t* init_host, int mode,
                 void* stream, uint64_t* level_sizes_host, uint32_t max_levels, reach_result* out);
 
+/* ------------------------------------------------------------------------ */
+/* Batched reachability: many independent models in one persistent launch.   */
+/* ------------------------------------------------------------------------ */
+
+/* Each model runs its own level-synchronous BFS (Alg. "Reachability
+ * analysis") on its own table, all inside one persistent kernel with no
+ * grid-wide barrier: warps claim work units (frontier rows, table-clear and
+ * re-insert chunks) from per-model claim words, and the warp that finishes a
+ * model's level advances that model alone.  Tables start at log2_initial[i]
+ * buckets (NULL or 0: an estimate -- twice the product of the local state
+ * counts when the model has no shared variables, capped at 2^16) and grow at
+ * a level boundary when the coming level could push them past 90% load: a new
+ * table from a device pool, sized for 50% load (never beyond the estimate's
+ * bound), the old one re-inserted.  Unlike the paper's fixed table (Section
+ * 3.1), this lets one launch serve models whose sizes are only estimated.
+ * Results are bit-identical to reach() on each model alone.
+ *
+ * pool_bytes must cover every model's initial table generation plus all
+ * growth (a generation of 2^n buckets takes 4*2^n + 3*16*ceil(W/4)*2^n bytes:
+ * buckets, data rows, two frontiers); a model whose growth does not fit ends
+ * with HT_ERR_OOM, the others are unaffected. */
+typedef struct reach_batch reach_batch_t;
+
+ht_status reach_batch_bytes(const reach_model* models, const int32_t* const* inits_host,
+                            int n_models, uint32_t max_levels, uint64_t pool_bytes,
+                            uint64_t* bytes);
+/* models/inits are host arrays of n_models entries; the block `mem_dev`
+ * (256-byte aligned, >= reach_batch_bytes) is owned by the caller.
+ * Synchronous (uploads the models). */
+ht_status reach_batch_create_at(const reach_model* models, const int32_t* const* inits_host,
+                                int n_models, const int32_t* log2_initial, uint32_t max_levels,
+                                uint64_t pool_bytes, const ht_params* params, void* mem_dev,
+                                uint64_t mem_bytes, reach_batch_t** out);
+ht_status reach_batch_create(const reach_model* models, const int32_t* const* inits_host,
+                             int n_models, const int32_t* log2_initial, uint32_t max_levels,
+                             uint64_t pool_bytes, const ht_params* params, reach_batch_t** out);
+ht_status reach_batch_destroy(reach_batch_t* b);
+
+/* Run the whole batch (reset + one persistent launch), asynchronously on
+ * `stream`.  use_graph = 1: the sequence is captured once into a CUDA graph and
+ * replayed by later calls (one graph launch per run). */
+ht_status reach_batch_run(reach_batch_t* b, int use_graph, void* stream);
+
+/* Wait for `stream` and copy per-model results to outs[n_models] (status per
+ * model), level sizes to level_sizes_host[n_models * max_levels] (may be
+ * NULL) and growth counts to grows[n_models] (may be NULL).  Returns the first
+ * error of any model, HT_OK when all succeeded. */
+ht_status reach_batch_results(reach_batch_t* b, void* stream, reach_result* outs,
+                              uint64_t* level_sizes_host, uint32_t* grows);
+
+/* Device time of the last reach_batch_run (CUDA events around it). */
+ht_status reach_batch_last_timing(reach_batch_t* b, float* ms);
+
 /* reach(model, init) for callers that cannot allocate device memory -- code
  * that must not call cudaMalloc (and so cannot create a context), e.g. a
  * process whose device memory is fixed at start-up.  There is no counterpart

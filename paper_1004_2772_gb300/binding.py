@@ -33,6 +33,8 @@ EXPORTED = [
     "reach_ctx_load", "reach_ctx_run", "reach_ctx_result", "reach_ctx_table", "reach",
     "reach_ctx_last_timing", "reach_ctx_level_ns", "vss_probe_random", "reach_noalloc",
     "vss_gen_keys", "ht_find_or_put_stream",
+    "reach_batch_bytes", "reach_batch_create", "reach_batch_create_at", "reach_batch_destroy",
+    "reach_batch_run", "reach_batch_results", "reach_batch_last_timing",
 ]
 
 
@@ -119,6 +121,15 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "vss_probe_random": [_VP, _u64, _u64, _i, _VP, ctypes.POINTER(ctypes.c_float)],
         "vss_gen_keys": [_u64, _u64, _u64, _u64, _VP, _i, _VP, _VP],
         "ht_find_or_put_stream": [_VP, _u64, _u64, _u64, _u64, _VP, _VP, _VP],
+        "reach_batch_bytes": [_VP, _VP, _i, ctypes.c_uint32, _u64, ctypes.POINTER(_u64)],
+        "reach_batch_create_at": [_VP, _VP, _i, _VP, ctypes.c_uint32, _u64, ctypes.POINTER(ht_params),
+                                  _VP, _u64, ctypes.POINTER(_VP)],
+        "reach_batch_create": [_VP, _VP, _i, _VP, ctypes.c_uint32, _u64, ctypes.POINTER(ht_params),
+                               ctypes.POINTER(_VP)],
+        "reach_batch_destroy": [_VP],
+        "reach_batch_run": [_VP, _i, _VP],
+        "reach_batch_results": [_VP, _VP, _VP, _VP, _VP],
+        "reach_batch_last_timing": [_VP, ctypes.POINTER(ctypes.c_float)],
         "reach_noalloc": [ctypes.POINTER(reach_model), _VP, _i, ctypes.POINTER(ht_params), _VP, _VP,
                           ctypes.c_uint32, ctypes.POINTER(reach_result)],
         "reach": [_VP, ctypes.POINTER(reach_model), _VP, _i, _VP, _VP, ctypes.c_uint32,
@@ -523,3 +534,98 @@ class ReachContext:
 
     def scan(self):
         return ht_scan(self.table_handle(), current_stream())
+
+
+# ---------------------------------------------------------------------------
+# Batched reachability (many models, one persistent launch).
+# ---------------------------------------------------------------------------
+
+def generation_bytes(log2_buckets: int, state_words: int) -> int:
+    """Bytes of one table generation: buckets, data rows and two frontiers."""
+    nb = 1 << log2_buckets
+    nv = (state_words + 3) // 4
+    up = lambda x: (x + 255) // 256 * 256
+    return up(4 * nb) + 3 * up(16 * nv * nb)
+
+
+def default_pool_bytes(models, log2_initial=None) -> int:
+    """Pool for the initial tables plus growth up to 50% load of each model's
+    state bound (product of local state counts when there are no shared
+    variables; otherwise 2^22 states is assumed)."""
+    total = 0
+    for i, m in enumerate(models):
+        bound = int(np.prod(np.asarray(m.n_local, dtype=np.float64))) if m.n_shared == 0 else 1 << 22
+        final = max(10, int(np.ceil(np.log2(max(bound, 1) / 0.5))))
+        init = (log2_initial[i] if log2_initial is not None and log2_initial[i] else min(final, 16))
+        g = generation_bytes(init, m.state_words)
+        lg = init
+        while lg < final:
+            lg += 1
+            g += generation_bytes(lg, m.state_words)
+        total += g
+    return total + (64 << 20)
+
+
+class ReachBatch:
+    """Many independent models expanded by one persistent kernel (optionally
+    replayed as a CUDA graph); device memory from a torch tensor."""
+
+    def __init__(self, models, log2_initial=None, max_levels: int = 4096, pool_bytes: int | None = None,
+                 device="cuda", **params):
+        torch = _torch()
+        self.models = list(models)
+        self.n = len(self.models)
+        self.max_levels = max_levels
+        self.params = make_params(**params)
+        self._args = [_ModelArgs(m) for m in self.models]
+        self._structs = (reach_model * self.n)(*[a.struct for a in self._args])
+        self._inits = (ctypes.c_void_p * self.n)(*[a.init.ctypes.data for a in self._args])
+        self._log2 = None
+        if log2_initial is not None:
+            self._log2 = np.ascontiguousarray(log2_initial, dtype=np.int32)
+        self.pool_bytes = pool_bytes or default_pool_bytes(self.models, log2_initial)
+        out = _u64()
+        _check(load().reach_batch_bytes(ctypes.byref(self._structs), ctypes.byref(self._inits), self.n,
+                                        max_levels, self.pool_bytes, ctypes.byref(out)), "reach_batch_bytes")
+        self.mem = torch.empty(out.value + 256, dtype=torch.uint8, device=device)
+        aligned = (self.mem.data_ptr() + 255) // 256 * 256
+        h = _VP()
+        _check(load().reach_batch_create_at(ctypes.byref(self._structs), ctypes.byref(self._inits), self.n,
+                                            self._log2.ctypes.data if self._log2 is not None else None,
+                                            max_levels, self.pool_bytes, ctypes.byref(self.params),
+                                            aligned, out.value, ctypes.byref(h)), "reach_batch_create_at")
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            load().reach_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, use_graph: bool = True):
+        _check(load().reach_batch_run(self.handle, int(use_graph), current_stream()), "reach_batch_run")
+
+    def last_timing(self) -> float:
+        ms = ctypes.c_float()
+        _check(load().reach_batch_last_timing(self.handle, ctypes.byref(ms)), "reach_batch_last_timing")
+        return ms.value
+
+    def results(self):
+        """(list of ReachOutput, grows per model, overall status)."""
+        outs = (reach_result * self.n)()
+        levels = np.zeros(self.n * self.max_levels, dtype=np.uint64)
+        grows = np.zeros(self.n, dtype=np.uint32)
+        st = load().reach_batch_results(self.handle, current_stream(), ctypes.byref(outs),
+                                        levels.ctypes.data, grows.ctypes.data)
+        res = []
+        for i in range(self.n):
+            r = outs[i]
+            lv = levels[i * self.max_levels:i * self.max_levels + min(r.n_levels, self.max_levels)]
+            res.append(ReachOutput(int(r.states), int(r.transitions), int(r.deadlocks), int(r.digest),
+                                   [int(x) for x in lv], int(r.busy_waits), int(r.rehashes), int(r.status)))
+        return res, [int(x) for x in grows], int(st)

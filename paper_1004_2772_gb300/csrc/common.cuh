@@ -249,6 +249,49 @@ __device__ __forceinline__ void load_row_cg(const uint4* row, Vec<NV>& v) {
   }
 }
 
+// Run-time row width (nv <= NV chunks; the rest of v is zero): used where one
+// kernel serves tables of different widths.
+template <int NV>
+__device__ __forceinline__ void load_row_rt(const uint4* row, Vec<NV>& v, uint32_t nv) {
+  if ((nv & 1u) == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; j += 2) {
+      if (j < (int)nv) ld_relaxed_v8(row + j, v.c[j], v.c[(j + 1) % NV]);
+      else v.c[j] = v.c[(j + 1) % NV] = make_uint4(0, 0, 0, 0);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v.c[j] = j < (int)nv ? ld_relaxed_v4(row + j) : make_uint4(0, 0, 0, 0);
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void load_row_cg_rt(const uint4* row, Vec<NV>& v, uint32_t nv) {
+  if ((nv & 1u) == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; j += 2) {
+      if (j < (int)nv) ld_cg_v8(row + j, v.c[j], v.c[(j + 1) % NV]);
+      else v.c[j] = v.c[(j + 1) % NV] = make_uint4(0, 0, 0, 0);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) v.c[j] = j < (int)nv ? __ldcg(row + j) : make_uint4(0, 0, 0, 0);
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void store_row_rt(uint4* row, const Vec<NV>& v, uint32_t nv) {
+  if ((nv & 1u) == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; j += 2)
+      if (j < (int)nv) st_v8(row + j, v.c[j], v.c[(j + 1) % NV]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      if (j < (int)nv) row[j] = v.c[j];
+  }
+}
+
 template <int NV>
 __device__ __forceinline__ void store_row(uint4* row, const Vec<NV>& v) {
   if (NV % 2 == 0) {

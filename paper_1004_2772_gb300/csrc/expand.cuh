@@ -1,0 +1,174 @@
+// Successor generation and one warp round of level expansion, shared by the
+// single-model drivers (reach.cu) and the batched driver (batch.cu).
+#pragma once
+
+#include "table.cuh"
+
+namespace vss {
+
+constexpr int kDescCap = 1024;  // successor descriptors per warp and round
+
+template <int NV>
+__host__ __device__ constexpr int row_stride() { return 4 * NV + 4; }  // padded: conflict-free 16 B reads
+
+__host__ __device__ constexpr int warp_smem_words_nv(int nv) { return 32 * (4 * nv + 4) + kDescCap + 32; }
+
+struct SModel {
+  int P, S, W, crit_any, maxfan, spw_max;
+  const int* base;
+  const int* crit;
+  const int* eb;
+  const int4* edges;
+  const int* uval;
+};
+
+struct Acc {
+  unsigned long long transitions = 0, deadlocks = 0, digest = 0, stored = 0;
+};
+
+template <int NV>
+__device__ __forceinline__ void vec_set(Vec<NV>& v, int i, uint32_t x) {
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    v.c[j].x = (4 * j + 0 == i) ? x : v.c[j].x;
+    v.c[j].y = (4 * j + 1 == i) ? x : v.c[j].y;
+    v.c[j].z = (4 * j + 2 == i) ? x : v.c[j].z;
+    v.c[j].w = (4 * j + 3 == i) ? x : v.c[j].w;
+  }
+}
+
+// One round of a level, warp-cooperatively and load-balanced over successors.
+//
+// The warp expands frontier rows [base, base + spw) (spw <= 32).  Phase 1:
+// lane i < spw reads state i's row, keeps it (and its hash sum) in shared
+// memory, and lists the enabled edges of the state (next-state) as
+// descriptors (edge | process << 24) in its own slice of the warp's
+// descriptor area; it counts the state's transitions and, when there are
+// none, a deadlock.  A warp scan of the counts gives T successors.  Phase 2:
+// lane j, j+32, ... builds successor j from its owner's row and the
+// descriptor and runs find-or-put -- so no lane serialises a whole fan-out.
+// New states are appended to the next frontier (rows) with one atomicAdd per
+// warp and iteration, straight from registers.
+// RT: rows have the table's run-time width t.nv (<= NV) instead of NV.
+template <int NV, int L, bool RT>
+__device__ __forceinline__ void expand_round(const TableView& t, const SModel& m, const uint4* cur,
+                                             uint32_t n_cur, uint64_t base, uint32_t spw,
+                                             uint4* next, uint32_t* next_count, uint32_t cap,
+                                             Acc& acc, LocalCounters& lc, uint32_t* wsm) {
+  constexpr int RS = row_stride<NV>();
+  uint32_t* rows = wsm;
+  uint32_t* desc = wsm + 32 * RS;
+  uint32_t* pref = desc + kDescCap;
+  const unsigned lane = lane_id();
+  const int P = m.P;
+  const int maxfan = m.maxfan;
+  const uint32_t nvr = RT ? t.nv : (uint32_t)NV;
+  // ---- phase 1: expand the round's states into successor descriptors
+  uint32_t c = 0;
+  const uint64_t f = base + lane;
+  if (lane < spw && f < n_cur) {
+    uint4* r = reinterpret_cast<uint4*>(rows + lane * RS);
+    Vec<NV> v;
+    if (RT) load_row_cg_rt<NV>(cur + f * nvr, v, nvr);
+    else load_row_cg<NV>(cur + f * NV, v);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) r[j] = v.c[j];
+    // the parent's hash sum, kept in the row's padding for its successors
+    const uint64_t hs = hash_sum(v, t.state_words, t.seed);
+    rows[lane * RS + 4 * NV] = (uint32_t)hs;
+    rows[lane * RS + 4 * NV + 1] = (uint32_t)(hs >> 32);
+    const int* rw = reinterpret_cast<const int*>(rows + lane * RS);
+    int ncrit = 0;
+    if (m.crit_any) {
+      for (int p = 0; p < P; ++p) {
+        const int cp = m.crit[p];
+        ncrit += (cp >= 0 && rw[p] == cp) ? 1 : 0;
+      }
+    }
+    uint32_t* d = desc + lane * maxfan;
+    for (int p = 0; p < P; ++p) {
+      const int s = rw[p];
+      const int b = m.base[p] + s;
+      const int cp = m.crit[p];
+      const int others = ncrit - ((cp >= 0 && s == cp) ? 1 : 0);
+      const int e_end = m.eb[b + 1];
+      for (int e = m.eb[b]; e < e_end; ++e) {
+        const int4 E = m.edges[e];
+        if (E.y >= 0 && rw[P + E.y] != E.z) continue;      // guard
+        if (cp >= 0 && E.x == cp && others > 0) continue;  // mutex
+        d[c++] = (uint32_t)e | ((uint32_t)p << 24);
+      }
+    }
+    acc.transitions += c;
+    if (c == 0) acc.deadlocks++;
+  }
+  uint32_t incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((int)lane >= o) incl += y;
+  }
+  pref[lane] = incl;
+  const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+  __syncwarp();
+  // ---- phase 2: one successor per lane per iteration; new states are
+  // appended to the next frontier (rows) with one atomicAdd per warp and
+  // iteration, straight from registers
+  const uint32_t iters = (T + 31) / 32;
+  for (uint32_t it = 0; it < iters; ++it) {
+    const uint32_t j = it * 32 + lane;
+    bool is_new = false;
+    Vec<NV> w;
+    if (j < T) {
+      uint32_t o = 0;  // owner = first lane whose inclusive prefix exceeds j
+#pragma unroll
+      for (uint32_t step = 16; step > 0; step >>= 1)
+        if (pref[o + step - 1] <= j) o += step;
+      const uint32_t k = j - (o ? pref[o - 1] : 0u);
+      const uint32_t dd = desc[o * maxfan + k];
+      const int e = (int)(dd & 0xFFFFFFu);
+      const int p = (int)(dd >> 24);
+      const int4 E = m.edges[e];
+      const uint32_t* ro = rows + o * RS;
+      const uint4* r = reinterpret_cast<const uint4*>(ro);
+#pragma unroll
+      for (int q = 0; q < NV; ++q) w.c[q] = r[q];
+      // successor hash from the parent's sum: only words p (and P + upd_var) change
+      uint64_t hs = (uint64_t)ro[4 * NV] | ((uint64_t)ro[4 * NV + 1] << 32);
+      hs += hash_term(t.seed, p, (uint32_t)E.x) - hash_term(t.seed, p, ro[p]);
+      vec_set(w, p, (uint32_t)E.x);
+      if (E.w >= 0) {
+        const int q = P + E.w;
+        const uint32_t uv = (uint32_t)m.uval[e];
+        hs += hash_term(t.seed, q, uv) - hash_term(t.seed, q, ro[q]);
+        vec_set(w, q, uv);
+      }
+      const uint64_t h = hash_final(hs, t.state_words);
+      uint32_t sidx = 0;
+      const int res = find_or_put<NV, L, RT>(t, w, h, sidx, lc);
+      if (res == FOP_NEW) {
+        is_new = true;
+        acc.digest += fingerprint(w, t.state_words);
+        acc.stored++;
+      }
+    }
+    const unsigned nb = __ballot_sync(0xffffffffu, is_new);
+    if (nb) {
+      uint32_t wbase = 0;
+      if (lane == 0) wbase = atomicAdd(next_count, (uint32_t)__popc(nb));
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (is_new) {
+        const uint32_t pos = wbase + __popc(nb & ((1u << lane) - 1u));
+        if (pos < cap) {
+          if (RT) store_row_rt<NV>(next + (size_t)pos * nvr, w, nvr);
+          else store_row<NV>(next + (size_t)pos * NV, w);
+        } else {
+          latch_error(t.ctr, HT_ERR_FULL);
+        }
+      }
+    }
+  }
+  __syncwarp();  // the warp's shared rows/descriptors are rewritten next round
+}
+
+}  // namespace vss

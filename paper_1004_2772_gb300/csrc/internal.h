@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 struct ht {
@@ -23,4 +25,8 @@ ht_status table_init_at(ht_t* h, int log2_nb, int max_words, const ht_params* pa
                         uint64_t mem_bytes);
 ht_status table_set_words(ht_t* h, int words);
 ht_status table_clear(ht_t* h, cudaStream_t s);
+// Validate a model and pack it (with init) into the device blob format;
+// blob header word [k]: see reach.cu.
+ht_status pack_model(const reach_model* m, const int32_t* init, int max_words,
+                     std::vector<int>& blob);
 }  // namespace vss

@@ -20,12 +20,11 @@
 #include <new>
 #include <vector>
 
+#include "expand.cuh"
 #include "internal.h"
-#include "table.cuh"
 
 namespace vss {
 
-constexpr int kDescCap = 1024;
 #ifndef VSS_REACH_MINB
 #define VSS_REACH_MINB 3  // __launch_bounds__ minimum resident blocks of the expansion kernels
 #endif             // successor descriptors per warp and round
@@ -39,20 +38,6 @@ constexpr int kHdr = 16;                   // blob header words
 //   [13] maxfan = sum over processes of the largest out-degree (bound on a state's successors)
 //   [14] spw_max = states per warp round, min(32, kDescCap / maxfan)
 // edges are int4 {dst, guard_var, guard_val, upd_var}; uval[e] = upd_val.
-template <int NV>
-__host__ __device__ constexpr int row_stride() { return 4 * NV + 4; }  // padded: conflict-free 16 B reads
-
-__host__ __device__ constexpr int warp_smem_words_nv(int nv) { return 32 * (4 * nv + 4) + kDescCap + 32; }
-
-struct SModel {
-  int P, S, W, crit_any, maxfan, spw_max;
-  const int* base;
-  const int* crit;
-  const int* eb;
-  const int4* edges;
-  const int* uval;
-};
-
 struct __align__(16) ReachTotals {
   unsigned long long transitions;
   unsigned long long deadlocks;
@@ -85,10 +70,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-struct Acc {
-  unsigned long long transitions = 0, deadlocks = 0, digest = 0, stored = 0;
-};
-
 __device__ __forceinline__ SModel load_model_smem(const ReachDev& rd, int* sm) {
   for (int i = threadIdx.x; i < rd.smem_words; i += blockDim.x) sm[i] = __ldg(rd.blob + i);
   __syncthreads();
@@ -107,44 +88,19 @@ __device__ __forceinline__ SModel load_model_smem(const ReachDev& rd, int* sm) {
   return m;
 }
 
-template <int NV>
-__device__ __forceinline__ void vec_set(Vec<NV>& v, int i, uint32_t x) {
-#pragma unroll
-  for (int j = 0; j < NV; ++j) {
-    v.c[j].x = (4 * j + 0 == i) ? x : v.c[j].x;
-    v.c[j].y = (4 * j + 1 == i) ? x : v.c[j].y;
-    v.c[j].z = (4 * j + 2 == i) ? x : v.c[j].z;
-    v.c[j].w = (4 * j + 3 == i) ? x : v.c[j].w;
-  }
-}
-
-// One level, warp-cooperatively and load-balanced over successors.
-//
-// A warp claims `spw` consecutive frontier states per round from a level
-// cursor (spw shrinks on small levels so that every warp gets work).  Phase 1: lane i < spw reads
-// state i's row, keeps it in shared memory, and lists the enabled edges of the
-// state (next-state) as descriptors (edge | process << 24) in its own slice
-// of the warp's descriptor area; it counts the state's transitions and, when
-// there are none, a deadlock.  A warp scan of the counts gives T successors.
-// Phase 2: lane j, j+32, ... builds successor j from its owner's row and the
-// descriptor, and runs find-or-put -- so no lane serialises a whole fan-out.
-// New indices are staged per lane and appended with one atomicAdd per round.
+// One level: a warp takes `spw` consecutive frontier states per round (spw
+// shrinks on small levels so that every warp gets work) and expands them with
+// expand_round.
 template <int NV, int L>
 __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, const uint4* cur,
                                           uint32_t n_cur, uint32_t* cursor, uint4* next,
                                           uint32_t* next_count, uint32_t cap, Acc& acc,
                                           LocalCounters& lc, uint32_t* wsm) {
-  constexpr int RS = row_stride<NV>();
-  uint32_t* rows = wsm;
-  uint32_t* desc = wsm + 32 * RS;
-  uint32_t* pref = desc + kDescCap;
   const unsigned lane = lane_id();
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t warps = gridDim.x * wpb;
   uint32_t spw = (n_cur + warps - 1) / warps;
   spw = spw < 1u ? 1u : (spw > (uint32_t)m.spw_max ? (uint32_t)m.spw_max : spw);
-  const int P = m.P;
-  const int maxfan = m.maxfan;
   const uint32_t warp_id = blockIdx.x * wpb + (threadIdx.x >> 5);
   const uint64_t static_rows = (uint64_t)warps * spw;
   for (bool first = true;; first = false) {
@@ -162,110 +118,7 @@ __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, c
       if (first) continue;
       break;
     }
-    // ---- phase 1: expand the round's states into successor descriptors
-    uint32_t c = 0;
-    const uint64_t f = base + lane;
-    if (lane < spw && f < n_cur) {
-      uint4* r = reinterpret_cast<uint4*>(rows + lane * RS);
-      Vec<NV> v;
-      load_row_cg<NV>(cur + f * NV, v);
-#pragma unroll
-      for (int j = 0; j < NV; ++j) r[j] = v.c[j];
-      // the parent's hash sum, kept in the row's padding for its successors
-      const uint64_t hs = hash_sum(v, t.state_words, t.seed);
-      rows[lane * RS + 4 * NV] = (uint32_t)hs;
-      rows[lane * RS + 4 * NV + 1] = (uint32_t)(hs >> 32);
-      const int* rw = reinterpret_cast<const int*>(rows + lane * RS);
-      int ncrit = 0;
-      if (m.crit_any) {
-        for (int p = 0; p < P; ++p) {
-          const int cp = m.crit[p];
-          ncrit += (cp >= 0 && rw[p] == cp) ? 1 : 0;
-        }
-      }
-      uint32_t* d = desc + lane * maxfan;
-      for (int p = 0; p < P; ++p) {
-        const int s = rw[p];
-        const int b = m.base[p] + s;
-        const int cp = m.crit[p];
-        const int others = ncrit - ((cp >= 0 && s == cp) ? 1 : 0);
-        const int e_end = m.eb[b + 1];
-        for (int e = m.eb[b]; e < e_end; ++e) {
-          const int4 E = m.edges[e];
-          if (E.y >= 0 && rw[P + E.y] != E.z) continue;      // guard
-          if (cp >= 0 && E.x == cp && others > 0) continue;  // mutex
-          d[c++] = (uint32_t)e | ((uint32_t)p << 24);
-        }
-      }
-      acc.transitions += c;
-      if (c == 0) acc.deadlocks++;
-    }
-    uint32_t incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if ((int)lane >= o) incl += y;
-    }
-    pref[lane] = incl;
-    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
-    __syncwarp();
-    // ---- phase 2: one successor per lane per iteration; new states are
-    // appended to the next frontier (rows) with one atomicAdd per warp and
-    // iteration, straight from registers
-    const uint32_t iters = (T + 31) / 32;
-    for (uint32_t it = 0; it < iters; ++it) {
-      const uint32_t j = it * 32 + lane;
-      bool is_new = false;
-      Vec<NV> w;
-      if (j < T) {
-        uint32_t o = 0;  // owner = first lane whose inclusive prefix exceeds j
-#pragma unroll
-        for (uint32_t step = 16; step > 0; step >>= 1)
-          if (pref[o + step - 1] <= j) o += step;
-        const uint32_t k = j - (o ? pref[o - 1] : 0u);
-        const uint32_t dd = desc[o * maxfan + k];
-        const int e = (int)(dd & 0xFFFFFFu);
-        const int p = (int)(dd >> 24);
-        const int4 E = m.edges[e];
-        const uint32_t* ro = rows + o * RS;
-        const uint4* r = reinterpret_cast<const uint4*>(ro);
-#pragma unroll
-        for (int q = 0; q < NV; ++q) w.c[q] = r[q];
-        // successor hash from the parent's sum: only words p (and P + upd_var) change
-        uint64_t hs = (uint64_t)ro[4 * NV] | ((uint64_t)ro[4 * NV + 1] << 32);
-        hs += hash_term(t.seed, p, (uint32_t)E.x) - hash_term(t.seed, p, ro[p]);
-        vec_set(w, p, (uint32_t)E.x);
-        if (E.w >= 0) {
-          const int q = P + E.w;
-          const uint32_t uv = (uint32_t)m.uval[e];
-          hs += hash_term(t.seed, q, uv) - hash_term(t.seed, q, ro[q]);
-          vec_set(w, q, uv);
-        }
-        const uint64_t h = hash_final(hs, t.state_words);
-        uint32_t sidx = 0;
-        const int res = find_or_put<NV, L>(t, w, h, sidx, lc);
-        if (res == FOP_NEW) {
-          is_new = true;
-          acc.digest += fingerprint(w, t.state_words);
-          acc.stored++;
-        }
-      }
-      const unsigned nb = __ballot_sync(0xffffffffu, is_new);
-      if (nb) {
-        uint32_t wbase = 0;
-        if (lane == 0) wbase = atomicAdd(next_count, (uint32_t)__popc(nb));
-        wbase = __shfl_sync(0xffffffffu, wbase, 0);
-        if (is_new) {
-          const uint32_t pos = wbase + __popc(nb & ((1u << lane) - 1u));
-          if (pos < cap) {
-            store_row<NV>(next + (size_t)pos * NV, w);
-          } else {
-            latch_error(t.ctr, HT_ERR_FULL);
-          }
-        }
-      }
-    }
-    __syncwarp();  // the warp's shared rows/descriptors are rewritten next round
+    expand_round<NV, L, false>(t, m, cur, n_cur, base, spw, next, next_count, cap, acc, lc, wsm);
   }
 }
 
@@ -488,8 +341,9 @@ static uint64_t ctx_bytes(int log2_nb, int max_words, uint32_t max_levels) {
          2 * align_up((uint64_t)max_levels * 8, 256);
 }
 
-static ht_status pack_model(const reach_model* m, const int32_t* init, int max_words,
-                            std::vector<int>& blob) {
+namespace vss {
+ht_status pack_model(const reach_model* m, const int32_t* init, int max_words,
+                     std::vector<int>& blob) {
   if (!m || !init) return HT_ERR_INVALID;
   const int P = m->n_procs, S = m->n_shared, W = m->state_words, E = m->n_edges;
   if (P < 1 || S < 0 || W < P + S || W > max_words || E < 0) return HT_ERR_INVALID;
@@ -564,6 +418,8 @@ static ht_status pack_model(const reach_model* m, const int32_t* init, int max_w
   for (int w = 0; w < W; ++w) blob[off_init + w] = init[w];
   return HT_OK;
 }
+
+}  // namespace vss
 
 static ReachDev make_rd(reach_ctx_t* c) {
   ReachDev rd;

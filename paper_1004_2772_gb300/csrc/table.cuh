@@ -60,12 +60,15 @@ struct LocalCounters {
 // reader that observed <memo, done> reads the data row only after an acquire
 // (an acquire load of the bucket, or an acquire fence after a relaxed load).
 // A CAS that returned <memo, done> is followed by the same fence.
-template <int NV>
+// RT = true: the row width is the table's run-time t.nv (<= NV), for kernels
+// that serve tables of several widths; otherwise it is exactly NV.
+template <int NV, bool RT>
 __device__ __forceinline__ bool data_equal_after_done(const TableView& t, uint32_t i,
                                                       const Vec<NV>& key, bool acquired) {
   if (!acquired) fence_acq_rel();
   Vec<NV> row;
-  load_row<NV>(t.data + (size_t)i * NV, row);
+  if (RT) load_row_rt<NV>(t.data + (size_t)i * t.nv, row, t.nv);
+  else load_row<NV>(t.data + (size_t)i * NV, row);
   return vec_eq(row, key);
 }
 
@@ -87,7 +90,7 @@ __device__ __forceinline__ bool wait_done(const TableView& t, uint32_t i, uint32
   return true;
 }
 
-template <int NV, int L>
+template <int NV, int L, bool RT = false>
 __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& key, uint64_t h,
                                         uint32_t& out_idx, LocalCounters& lc) {
   static_assert(L == 8 || L == 16 || L == 32, "line of 8, 16 or 32 buckets");
@@ -146,7 +149,8 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
         if (b == 0u) {
           const uint32_t old = atomicCAS(t.buckets + i, 0u, memo);  // <memo, write>
           if (old == 0u) {
-            store_row<NV>(t.data + (size_t)i * NV, key);
+            if (RT) store_row_rt<NV>(t.data + (size_t)i * t.nv, key, t.nv);
+            else store_row<NV>(t.data + (size_t)i * NV, key);
             fence_acq_rel();                 // data before <memo, done>
             st_relaxed(t.buckets + i, memo | kDone);
             out_idx = i;
@@ -162,7 +166,7 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
             if (!wait_done(t, i, b, lc)) return FOP_ERR;
             acquired = true;
           }
-          if (data_equal_after_done<NV>(t, i, key, acquired)) {
+          if (data_equal_after_done<NV, RT>(t, i, key, acquired)) {
             out_idx = i;
             return FOP_SEEN;
           }
