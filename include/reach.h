@@ -309,6 +309,54 @@ ht_status reach_batch_results(reach_batch_t* b, void* stream, reach_result* outs
 /* Device time of the last reach_batch_run (CUDA events around it). */
 ht_status reach_batch_last_timing(reach_batch_t* b, float* ms);
 
+/* ------------------------------------------------------------------------ */
+/* Served reachability: a request loop with continuous batching.              */
+/* ------------------------------------------------------------------------ */
+
+/* One persistent kernel (the batched driver in serving mode) runs while jobs
+ * arrive.  serve_submit queues a job; a job is admitted when one of n_slots
+ * slots is free and its memory fits in the arena (the HBM budget: table
+ * generation of 2^log2 buckets plus the packed model, see reach_batch); the
+ * host then posts it through the slot's host-mapped mailbox and a device warp
+ * with no work takes it, so it overlaps with the jobs already running.  A
+ * finished job is returned by serve_poll and its memory freed, which may admit
+ * queued jobs.  Each job's result equals reach() on it alone.  The kernel
+ * leaves after ~0.1 s without work (all device waits are bounded) and is
+ * relaunched by the next submit or poll.  One host thread at a time. */
+typedef struct serve serve_t;
+
+typedef struct {
+  uint64_t job_id;
+  reach_result result;   /* status HT_ERR_OOM: the job can never fit the arena */
+  uint32_t grows;
+  uint32_t pad;
+  double submit_s;       /* host steady-clock seconds: submitted, admitted, seen done */
+  double admit_s;
+  double done_s;
+} serve_done_t;
+
+ht_status serve_bytes(uint64_t budget_bytes, uint32_t n_slots, uint32_t max_levels,
+                      uint64_t* bytes);
+/* mem_dev (256-byte aligned) of at least serve_bytes(); the arena is what
+ * remains after the slot records.  Synchronous. */
+ht_status serve_open_at(void* mem_dev, uint64_t mem_bytes, uint32_t n_slots, uint32_t max_levels,
+                        const ht_params* params, serve_t** out);
+ht_status serve_open(uint64_t budget_bytes, uint32_t n_slots, uint32_t max_levels,
+                     const ht_params* params, serve_t** out);
+/* Queue a job (host model and init are copied; the call returns at once).
+ * log2_buckets 0: sized for 75% load of the product of the local state counts
+ * (models without shared variables only). */
+ht_status serve_submit(serve_t* s, const reach_model* m, const int32_t* init_host, int log2_buckets,
+                       uint64_t* job_id);
+/* Collect up to max_done finished jobs (and their level sizes, max_levels per
+ * job, into level_sizes_host when not NULL); admits queued jobs. */
+ht_status serve_poll(serve_t* s, serve_done_t* done, uint32_t max_done, uint32_t* n_done,
+                     uint64_t* level_sizes_host);
+ht_status serve_status(serve_t* s, uint32_t* queued, uint32_t* running, uint64_t* free_bytes,
+                       uint64_t* kernel_launches);
+/* Stop accepting, wait for running jobs, release everything. */
+ht_status serve_close(serve_t* s);
+
 /* reach(model, init) for callers that cannot allocate device memory -- code
  * that must not call cudaMalloc (and so cannot create a context), e.g. a
  * process whose device memory is fixed at start-up.  There is no counterpart

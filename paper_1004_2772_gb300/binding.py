@@ -35,6 +35,8 @@ EXPORTED = [
     "vss_gen_keys", "ht_find_or_put_stream",
     "reach_batch_bytes", "reach_batch_create", "reach_batch_create_at", "reach_batch_destroy",
     "reach_batch_run", "reach_batch_results", "reach_batch_last_timing",
+    "serve_bytes", "serve_open_at", "serve_open", "serve_submit", "serve_poll", "serve_status",
+    "serve_close",
 ]
 
 
@@ -130,6 +132,16 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "reach_batch_run": [_VP, _i, _VP],
         "reach_batch_results": [_VP, _VP, _VP, _VP, _VP],
         "reach_batch_last_timing": [_VP, ctypes.POINTER(ctypes.c_float)],
+        "serve_bytes": [_u64, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(_u64)],
+        "serve_open_at": [_VP, _u64, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ht_params),
+                          ctypes.POINTER(_VP)],
+        "serve_open": [_u64, ctypes.c_uint32, ctypes.c_uint32, ctypes.POINTER(ht_params),
+                       ctypes.POINTER(_VP)],
+        "serve_submit": [_VP, ctypes.POINTER(reach_model), _VP, _i, ctypes.POINTER(_u64)],
+        "serve_poll": [_VP, _VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32), _VP],
+        "serve_status": [_VP, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
+                         ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
+        "serve_close": [_VP],
         "reach_noalloc": [ctypes.POINTER(reach_model), _VP, _i, ctypes.POINTER(ht_params), _VP, _VP,
                           ctypes.c_uint32, ctypes.POINTER(reach_result)],
         "reach": [_VP, ctypes.POINTER(reach_model), _VP, _i, _VP, _VP, ctypes.c_uint32,
@@ -629,3 +641,88 @@ class ReachBatch:
             res.append(ReachOutput(int(r.states), int(r.transitions), int(r.deadlocks), int(r.digest),
                                    [int(x) for x in lv], int(r.busy_waits), int(r.rehashes), int(r.status)))
         return res, [int(x) for x in grows], int(st)
+
+
+# ---------------------------------------------------------------------------
+# Serving (continuous batching of reachability jobs).
+# ---------------------------------------------------------------------------
+
+class serve_done_t(ctypes.Structure):
+    _fields_ = [("job_id", ctypes.c_uint64), ("result", reach_result), ("grows", ctypes.c_uint32),
+                ("pad", ctypes.c_uint32), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("done_s", ctypes.c_double)]
+
+
+@dataclass
+class ServedJob:
+    job_id: int
+    result: ReachOutput
+    submit_s: float
+    admit_s: float
+    done_s: float
+
+    @property
+    def latency_s(self) -> float:
+        return self.done_s - self.submit_s
+
+
+class Server:
+    """Reachability request loop: jobs are admitted by HBM budget into slots of
+    one persistent kernel (continuous batching); arena memory from torch."""
+
+    def __init__(self, budget_bytes: int, n_slots: int = 64, max_levels: int = 4096, device="cuda",
+                 **params):
+        torch = _torch()
+        self.max_levels = max_levels
+        self.params = make_params(**params)
+        out = _u64()
+        _check(load().serve_bytes(budget_bytes, n_slots, max_levels, ctypes.byref(out)), "serve_bytes")
+        self.mem = torch.empty(out.value + 256, dtype=torch.uint8, device=device)
+        aligned = (self.mem.data_ptr() + 255) // 256 * 256
+        h = _VP()
+        _check(load().serve_open_at(aligned, out.value, n_slots, max_levels, ctypes.byref(self.params),
+                                    ctypes.byref(h)), "serve_open_at")
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, model, log2_buckets: int = 0) -> int:
+        a = _ModelArgs(model)
+        jid = _u64()
+        _check(load().serve_submit(self.handle, ctypes.byref(a.struct), a.init.ctypes.data, log2_buckets,
+                                   ctypes.byref(jid)), "serve_submit")
+        return jid.value
+
+    def poll(self, max_done: int = 256, want_levels: bool = True):
+        done = (serve_done_t * max_done)()
+        n = ctypes.c_uint32()
+        levels = np.zeros(max_done * self.max_levels, dtype=np.uint64) if want_levels else None
+        _check(load().serve_poll(self.handle, ctypes.byref(done), max_done, ctypes.byref(n),
+                                 levels.ctypes.data if levels is not None else None), "serve_poll")
+        out = []
+        for i in range(n.value):
+            d = done[i]
+            r = d.result
+            lv = []
+            if levels is not None:
+                lv = [int(x) for x in levels[i * self.max_levels:i * self.max_levels + min(r.n_levels, self.max_levels)]]
+            out.append(ServedJob(int(d.job_id), ReachOutput(int(r.states), int(r.transitions), int(r.deadlocks),
+                                                            int(r.digest), lv, int(r.busy_waits), int(r.rehashes),
+                                                            int(r.status)), d.submit_s, d.admit_s, d.done_s))
+        return out
+
+    def status(self):
+        q, r, f, k = ctypes.c_uint32(), ctypes.c_uint32(), _u64(), _u64()
+        _check(load().serve_status(self.handle, ctypes.byref(q), ctypes.byref(r), ctypes.byref(f),
+                                   ctypes.byref(k)), "serve_status")
+        return {"queued": q.value, "running": r.value, "free_bytes": f.value, "kernel_launches": k.value}
+
+    def close(self):
+        if self.handle:
+            _check(load().serve_close(self.handle), "serve_close")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -26,64 +26,11 @@
 #include <new>
 #include <vector>
 
+#include "batch.h"
 #include "expand.cuh"
 #include "internal.h"
 
 namespace vss {
-
-enum : uint32_t { PH_CLEAR = 0, PH_EXPAND = 1, PH_REHASH = 2, PH_DONE = 3 };
-
-constexpr uint32_t kClearUnit = 8192;   // buckets zeroed per unit (256 per lane)
-constexpr uint32_t kRehashUnit = 1024;  // old buckets re-inserted per unit (32 per lane)
-constexpr uint32_t kCopyUnit = 32;      // frontier rows copied per unit (one per lane)
-constexpr int kBatchNV = 8;             // state vectors up to 32 words
-constexpr uint32_t kUnitsMax = (1u << 24) - 1;
-
-struct __align__(16) BatchModel {
-  const int* blob;                  // packed model (global memory)
-  unsigned long long* level_sizes;  // [max_levels]
-  uint32_t W, nv, maxfan, spw_max;
-  uint32_t max_levels;
-  uint32_t log2_nb;                 // current table
-  uint32_t* buckets;
-  uint4* data;
-  uint4* fr[2];                     // frontier rows of the current table's capacity
-  uint32_t* nbuckets;               // table being built (CLEAR / REHASH), or the initial table
-  uint4* ndata;
-  uint4* nfr[2];
-  uint32_t nlog2;
-  uint32_t cur;                     // frontier holding the current level
-  unsigned long long claim;         // see the file comment
-  uint32_t done[2];
-  uint32_t next_count[2];
-  uint32_t n_cur;                   // rows of fr[cur]
-  uint32_t level;                   // index of the level in fr[cur]
-  uint32_t n_rehash_b;              // REHASH units below this are bucket units
-  uint32_t grows;
-  unsigned long long states_bound;  // upper bound on the model's states (0 = unknown)
-  DevCounters ctr;                  // err, stored, busy_waits, rehashes
-  unsigned long long transitions, deadlocks, digest;
-  uint32_t n_levels, finished;
-};
-
-struct BatchState {
-  unsigned long long pool_used;
-  uint32_t finished;
-  uint32_t err;
-};
-
-struct BatchGlobal {
-  BatchModel* models;
-  BatchState* st;
-  char* pool;
-  unsigned long long pool_bytes;
-  uint64_t seed;
-  uint32_t n_models;
-  uint32_t max_spin;
-  uint32_t idle_limit;
-  float grow_at;                    // grow when the coming level could pass this load factor
-  float grow_to;                    // load factor the grown table is sized for
-};
 
 __device__ __forceinline__ unsigned long long pack_claim(uint32_t epoch, uint32_t phase,
                                                          uint32_t units, uint32_t claimed) {
@@ -161,10 +108,32 @@ __device__ __forceinline__ SModel model_view(const int* blob) {
 
 __device__ __forceinline__ uint64_t align256(uint64_t x) { return (x + 255) & ~255ull; }
 
-// Bytes of one table generation: buckets, data rows, two frontiers.
-__host__ __device__ __forceinline__ uint64_t generation_bytes(uint32_t log2, uint32_t nv) {
-  const uint64_t nb = 1ull << log2;
-  return ((nb * 4 + 255) & ~255ull) + 3 * ((nb * 16 * nv + 255) & ~255ull);
+__device__ __forceinline__ unsigned long long ld_acquire_sys64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_sys32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_sys64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 __device__ void finish_model(BatchModel& M, const BatchGlobal& g, uint32_t epoch, uint32_t status) {
@@ -172,7 +141,60 @@ __device__ void finish_model(BatchModel& M, const BatchGlobal& g, uint32_t epoch
   M.finished = 1;
   __threadfence();
   atomicExch(&M.claim, pack_claim(epoch + 1, PH_DONE, 0, 0));
-  atomicAdd(&g.st->finished, 1u);
+  if (!g.mb) {
+    atomicAdd(&g.st->finished, 1u);
+    return;
+  }
+  // serving: hand the result to the host through the slot's mapped mailbox
+  const uint32_t s = (uint32_t)(&M - g.models);
+  volatile ServeSlotOut* o = g.out + s;
+  o->states = ldm(M.ctr.stored);
+  o->transitions = ldm(M.transitions);
+  o->deadlocks = ldm(M.deadlocks);
+  o->digest = ldm(M.digest);
+  o->busy_waits = ldm(M.ctr.busy_waits);
+  o->rehashes = ldm(M.ctr.rehashes);
+  o->n_levels = ldm(M.n_levels);
+  o->status = ldm(M.ctr.err);
+  o->grows = ldm(M.grows);
+  __threadfence_system();
+  st_release_sys64(&g.out[s].seq, ldm(g.accepted[s]));
+  atomicSub(&g.st->active, 1u);
+}
+
+// Serving: take the jobs the host posted since the last scan into their slots.
+// Run by one thread of a warp that found no work.  Returns whether it
+// activated any job.
+__device__ bool serve_accept(const BatchGlobal& g) {
+  const unsigned long long db = ld_acquire_sys64(&g.mb->doorbell);
+  if (db == ld_relaxed64(&g.st->seen_doorbell)) return false;
+  if (atomicCAS(&g.st->scan_lock, 0u, 1u) != 0u) return false;
+  const unsigned long long db2 = ld_acquire_sys64(&g.mb->doorbell);
+  bool any = false;
+  constexpr int kWords = sizeof(BatchModel) / 8;
+  constexpr int kClaimWord = offsetof(BatchModel, claim) / 8;
+  for (uint32_t s = 0; s < g.n_models; ++s) {
+    const unsigned long long seq = ld_acquire_sys64(&g.in[s].seq);
+    if (seq == ldm(g.accepted[s])) continue;
+    // the host reuses a slot only after it saw the slot's last job finish
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&g.in[s].rec);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&g.models[s]);
+    unsigned long long claim = 0;
+    for (int i = 0; i < kWords; ++i) {
+      const unsigned long long w = ld_relaxed_sys64(src + i);
+      if (i == kClaimWord) claim = w;
+      else dst[i] = w;
+    }
+    g.accepted[s] = seq;
+    atomicAdd(&g.st->active, 1u);
+    __threadfence();
+    atomicExch(&g.models[s].claim, claim);
+    any = true;
+  }
+  st_relaxed64(&g.st->seen_doorbell, db2);
+  __threadfence();
+  atomicExch(&g.st->scan_lock, 0u);
+  return any;
 }
 
 __device__ void publish(BatchModel& M, uint32_t epoch, uint32_t phase, uint32_t units) {
@@ -294,9 +316,11 @@ __global__ void __launch_bounds__(256, 2) k_reach_batch(BatchGlobal g) {
   const unsigned lane = lane_id();
   const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const uint32_t n = g.n_models;
-  uint32_t rot = gw * 2654435761u, idle = 0;
+  uint32_t rot = gw * 2654435761u, idle = 0, nap = 64;
+  unsigned long long idle_since = 0;
   for (;;) {
-    if (ld_relaxed(&g.st->finished) >= n || ld_relaxed(&g.st->err)) break;
+    if (ld_relaxed(&g.st->err)) break;
+    if (!g.mb && ld_relaxed(&g.st->finished) >= n) break;
     // find a model with unclaimed units: 32 models per step, one per lane
     int m = -1;
     for (uint32_t b = 0; b < n && m < 0; b += 32) {
@@ -311,14 +335,44 @@ __global__ void __launch_bounds__(256, 2) k_reach_batch(BatchGlobal g) {
       if (ball) m = (int)__shfl_sync(0xffffffffu, mi, __ffs(ball) - 1);
     }
     if (m < 0) {
-      if (++idle > g.idle_limit) {
+      // no claimable work: back off (up to ~16 us between looks); every wait
+      // here is bounded in time by idle_ns
+      if (idle++ == 0) idle_since = global_ns();
+      const bool idle_long = global_ns() - idle_since > g.idle_ns;
+      if (g.mb) {
+        // serving: look for newly posted jobs; leave when nothing is running
+        // and the host asked to shut down or nothing arrived for idle_ns (the
+        // host relaunches the kernel on its next submission)
+        int took = 0, leave = 0;
+        if (lane == 0) {
+          took = serve_accept(g) ? 1 : 0;
+          if (!took && ld_relaxed(&g.st->active) == 0) {
+            const bool stop = ld_acquire_sys32(&g.mb->shutdown) != 0u;
+            const bool posted = ld_acquire_sys64(&g.mb->doorbell) != ld_relaxed64(&g.st->seen_doorbell);
+            leave = !posted && (stop || idle_long);
+          } else if (!took && global_ns() - idle_since > g.stuck_ns) {
+            atomicCAS(&g.st->err, 0u, (uint32_t)HT_ERR_TIMEOUT);
+            leave = 1;
+          }
+        }
+        took = __shfl_sync(0xffffffffu, took, 0);
+        leave = __shfl_sync(0xffffffffu, leave, 0);
+        if (leave) break;
+        if (took) {
+          idle = 0;
+          nap = 64;
+          continue;
+        }
+      } else if (global_ns() - idle_since > g.stuck_ns) {
         if (lane == 0) atomicCAS(&g.st->err, 0u, (uint32_t)HT_ERR_TIMEOUT);
         break;
       }
-      __nanosleep(128);
+      __nanosleep(nap);
+      nap = nap < 16384 ? nap * 2 : nap;
       continue;
     }
     idle = 0;
+    nap = 64;
     rot = rot * 1664525u + 1013904223u;
     BatchModel& M = g.models[m];
     // claim: rows of an EXPAND level (several at a time), single units otherwise
@@ -416,14 +470,16 @@ __global__ void __launch_bounds__(256, 2) k_reach_batch(BatchGlobal g) {
   }
 }
 
-using BatchKernel = void (*)(BatchGlobal);
-
-static BatchKernel pick_batch(int L) {
+BatchKernel batch_kernel(int L) {
   switch (L) {
     case 8: return k_reach_batch<8>;
     case 16: return k_reach_batch<16>;
     default: return k_reach_batch<32>;
   }
+}
+
+size_t batch_smem_bytes(int threads) {
+  return (size_t)(threads / 32) * warp_smem_words_nv(kBatchNV) * 4;
 }
 
 static uint64_t up256(uint64_t x) { return (x + 255) & ~255ull; }
@@ -593,9 +649,9 @@ ht_status reach_batch_create_at(const reach_model* models, const int32_t* const*
   std::memset(b->state_init_pinned, 0, sizeof(BatchState));
   b->state_init_pinned->pool_used = pool_used;
 
-  b->kernel = pick_batch((int)p.line_buckets);
+  b->kernel = batch_kernel((int)p.line_buckets);
   b->threads = 256;
-  b->smem = (size_t)(b->threads / 32) * warp_smem_words_nv(kBatchNV) * 4;
+  b->smem = batch_smem_bytes(b->threads);
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
@@ -611,7 +667,8 @@ ht_status reach_batch_create_at(const reach_model* models, const int32_t* const*
   b->g.seed = p.hash_seed;
   b->g.n_models = (uint32_t)n_models;
   b->g.max_spin = p.max_spin;
-  b->g.idle_limit = 1u << 22;
+  b->g.idle_ns = 0;
+  b->g.stuck_ns = 4000000000ull;  // 4 s with no claimable work while models are unfinished
   b->g.grow_at = 0.9f;
   b->g.grow_to = 0.5f;
   *out = b;

@@ -335,3 +335,25 @@ def call_ids(seed: int, n_ids: int, start: int, count: int, dist: str = "uniform
     else:
         raise ValueError(dist)
     return np.where(odd, dup, i).astype(np.uint64)
+
+
+# ---------------------------------------------------------------------------
+# Served reachability: a Poisson stream of interleaving-family jobs.
+# ---------------------------------------------------------------------------
+
+def served_jobs(seed: int = 5, rate: float = 20.0, duration_s: float = 10.0, lo: float = 1e4,
+                hi: float = 2e8, state_words: int = 16, max_jobs: int | None = None):
+    """[(arrival_s, model)]: exponential inter-arrival gaps of mean 1/rate,
+    target sizes log-uniform in [lo, hi], P = uniform(3, 8) processes."""
+    rng = SplitMix64(seed)
+    t, out, k = 0.0, [], 0
+    while True:
+        t += -math.log(1.0 - rng.unit()) / rate
+        if t > duration_s or (max_jobs is not None and len(out) >= max_jobs):
+            break
+        target = int(round(10 ** (math.log10(lo) + (math.log10(hi) - math.log10(lo)) * rng.unit())))
+        P = rng.uniform(3, 8)
+        k += 1
+        out.append((t, sized_interleaving_model(seed * 100003 + k, P, state_words, target,
+                                                name=f"served-{seed}-{k}")))
+    return out
