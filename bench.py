@@ -27,6 +27,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -38,6 +40,10 @@ WORKLOADS = {
     "beem": (dict(seed=22, update_pct=40), 26),
     "beem-medium": (dict(seed=7, update_pct=40), 24),
     "tiny": (None, 18),
+    # not reachability of one model: see run_hashtable / run_batch / run_serve
+    "hashtable": (None, 26),
+    "batch": (None, 0),
+    "serve": (None, 0),
 }
 LOG2_BUCKETS = 26
 MAX_LEVELS = 1 << 14
@@ -60,7 +66,7 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -77,7 +83,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -231,7 +237,7 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="persistent", choices=["persistent", "per-level"])
@@ -239,6 +245,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="beem", choices=sorted(WORKLOADS))
     ap.add_argument("--log2-buckets", type=int, default=0, help="0 = the workload's size")
+    ap.add_argument("--load-factor", type=float, default=0.75, help="hashtable: keys / buckets")
+    ap.add_argument("--dist", default="uniform", choices=["uniform", "zipf"], help="hashtable reuse")
+    ap.add_argument("--key-mode", default="fused", choices=["fused", "api"],
+                    help="hashtable: keys generated in registers, or materialised batches")
+    ap.add_argument("--autotune", action="store_true", help="hashtable: tune parameters first")
+    ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     args = ap.parse_args()
     global LOG2_BUCKETS
     LOG2_BUCKETS = args.log2_buckets or WORKLOADS[args.workload][1]
@@ -253,6 +265,10 @@ def main():
     dev = torch.device("cuda", local)
     _build.build()
     binding.load()
+    if args.workload in ("hashtable", "batch", "serve"):
+        {"hashtable": run_hashtable, "batch": run_batch, "serve": run_serve}[args.workload](
+            args, world, rank, local, dev)
+        return
 
     # random-access rates of this GPU (the random-sector roofline's denominators)
     rates = binding.random_access_rates(gib=16, n_access=1 << 28)
@@ -347,6 +363,173 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+
+def base_line(args, world, metric, value, unit, ms_per_step, config, higher=True):
+    return {"metric": metric, "value": value, "unit": unit, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": higher,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config}
+
+
+def run_hashtable(args, world, rank, local, dev):
+    """Hash-table benchmark: one step = one fill of a 2^n table to the load
+    factor (2 * LF * 2^n find-or-put calls, half of them repeating an earlier
+    key uniformly or by Zipf(1.1)); value = find-or-put calls per second."""
+    import torch
+    from paper_1004_2772_gb300 import autotune, binding, synth
+    log2, lf = LOG2_BUCKETS, args.load_factor
+    n_ids = int(lf * (1 << log2))
+    calls = 2 * n_ids
+    zipf = synth.zipf_table(n_ids) if args.dist == "zipf" else None
+    params = {"line_buckets": args.line_buckets}
+    tuned = None
+    if args.autotune:
+        tuned = autotune.tune_table(log2, lf, args.dist, cache_path=None)
+        params = dict(tuned["best"])
+    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
+    tab = binding.Table(log2, 16, **params)
+    keys = None
+    if args.key_mode == "api":
+        keys = tab.gen_keys(1, n_ids, 0, calls, zipf)
+    def step():
+        tab.clear()
+        if keys is None:
+            return tab.find_or_put_stream(1, n_ids, 0, calls, zipf, sync=False)
+        return tab.find_or_put(keys, want_idx=True)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    with ClockSampler(local) as clocks:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            out = step()
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the last fill must have stored exactly the fill's distinct keys
+    st = tab.stats()
+    assert st.stored == n_ids and st.error == 0, (st.stored, n_ids)
+    t_max = max_over_ranks(ms, world, dev)
+    ops = sum_over_ranks(float(calls), world, dev) / (t_max / 1e3)
+    dup, new = calls - n_ids, n_ids
+    alg = calls * 32 + dup * 64 + new * (64 + 32) + (calls * (64 + 5) if keys is not None else 0)
+    peak, which = peaks()
+    bound_s = calls / rates[0] + dup / rates[1] + 3 * new / rates[2]
+    line = base_line(args, world, "find_or_put ops/sec on 1 GB300 (hash-table benchmark)", ops,
+                     "find_or_put/s", t_max,
+                     {"workload": f"hashtable-W16-2^{log2}-lf{lf}-{args.dist}-{args.key_mode}",
+                      "calls_per_step": calls, "distinct_keys": n_ids, "params": params,
+                      "l2": "inputs larger than L2 (table 4.3 GB at 2^26)"})
+    line["roofline"] = {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
+                        "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None,
+                        "algorithmic_bytes": alg, "peak_source": which}
+    line["random_roofline"] = {"bound_ms": bound_s * 1e3, "frac": bound_s * 1e3 / ms,
+                               "probe_rates_per_s": {"read32": rates[0], "read64": rates[1],
+                                                     "write32": rates[2], "atomic32": rates[3]}}
+    line["gpu_launches"] = args.steps * (1 if keys is None else 1)
+    line["clocks"] = clocks.summary()
+    if tuned:
+        line["autotune"] = {"best": tuned["best"], "candidates": len(tuned["all"])}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_batch(args, world, rank, local, dev):
+    """Batched reachability: one step = the 256 seeded interleaving models of
+    uneven size (3-12 processes, 8-32 words, 10^3-10^6 states) in one
+    persistent launch replayed as a CUDA graph; compared with one model per
+    launch."""
+    import torch
+    from paper_1004_2772_gb300 import binding, synth
+    models = synth.batched_models(count=256, first_seed=1)
+    bt = binding.ReachBatch(models, max_levels=4096)
+    for _ in range(max(3, args.warmup)):
+        bt.run(use_graph=True)
+    ref, grows, st = bt.results()
+    assert st == 0
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            bt.run(use_graph=True)
+        e1.record()
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    got, grows, st = bt.results()
+    assert st == 0 and [r.digest for r in got] == [r.digest for r in ref]
+    states = sum(r.states for r in got)
+    # one model per launch (the plain path), contexts sized per model
+    ctxs, t0 = {}, time.perf_counter()
+    for m in models:
+        lg = max(10, int(np.ceil(np.log2(float(np.prod(m.n_local)) / 0.5))))
+        ctxs.setdefault(lg, binding.ReachContext(lg, 32, max_levels=4096))
+        ctxs[lg].reach(m)
+    torch.cuda.synchronize()
+    loop_ms = (time.perf_counter() - t0) * 1e3
+    t_max = max_over_ranks(ms, world, dev)
+    value = sum_over_ranks(float(states), world, dev) / (t_max / 1e3)
+    line = base_line(args, world, "states/sec on 1 GB300 (batched reachability, 256 models)", value,
+                     "states/s", t_max,
+                     {"workload": "batched-256-interleaving-models", "models": len(models),
+                      "states": states, "table_grows": sum(grows), "graph": True,
+                      "l2": "inputs larger than L2 (tables and frontiers, GBs)"})
+    line["one_model_per_launch"] = {"ms": loop_ms, "states_per_s": states / (loop_ms / 1e3)}
+    line["gpu_launches"] = args.steps
+    line["clocks"] = clocks.summary()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serve(args, world, rank, local, dev):
+    """Served reachability: a Poisson stream (20 jobs/s) of interleaving jobs of
+    log-uniform size 10^4..2*10^8 states (W = 16) submitted in real time to the
+    continuous-batching server (HBM budget = 85% of free memory); reports
+    aggregate states/s and p50/p99 latency, and the same stream with one slot
+    (jobs one at a time)."""
+    import torch
+    from paper_1004_2772_gb300 import binding, synth
+    jobs = synth.served_jobs(seed=5, rate=20.0, duration_s=args.duration)
+    free, _ = torch.cuda.mem_get_info()
+    out = {}
+    for slots in (64, 1):
+        srv = binding.Server(budget_bytes=int(free * 0.85), n_slots=slots, max_levels=4096)
+        srv.submit(jobs[0][1])
+        while not srv.poll(want_levels=False):
+            time.sleep(0.001)
+        done, k, t0 = [], 0, time.perf_counter()
+        while len(done) < len(jobs):
+            now = time.perf_counter() - t0
+            while k < len(jobs) and jobs[k][0] <= now:
+                srv.submit(jobs[k][1])
+                k += 1
+            done += srv.poll(want_levels=False)
+            time.sleep(0.0005)
+        span = time.perf_counter() - t0
+        lat = np.array([d.latency_s for d in done]) * 1e3
+        assert all(d.result.status == 0 for d in done)
+        out[slots] = {"span_s": span, "states": sum(d.result.states for d in done),
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "max_ms": float(lat.max()), "kernel_launches": srv.status()["kernel_launches"]}
+        srv.close()
+        del srv
+        torch.cuda.empty_cache()
+    c = out[64]
+    line = base_line(args, world, "states/sec on 1 GB300 (served reachability, Poisson 20 jobs/s)",
+                     c["states"] / c["span_s"], "states/s", c["span_s"] * 1e3 / max(1, len(jobs)),
+                     {"workload": f"served-poisson20-{len(jobs)}jobs-1e4..2e8-W16", "slots": 64,
+                      "jobs": len(jobs)})
+    line["latency_ms"] = {"p50": c["p50_ms"], "p99": c["p99_ms"], "max": c["max_ms"]}
+    line["one_job_at_a_time"] = {"p50_ms": out[1]["p50_ms"], "p99_ms": out[1]["p99_ms"],
+                                 "states_per_s": out[1]["states"] / out[1]["span_s"]}
+    line["gpu_launches"] = c["kernel_launches"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 if __name__ == "__main__":
