@@ -47,6 +47,10 @@ WORKLOADS = {
 }
 LOG2_BUCKETS = 26
 MAX_LEVELS = 1 << 14
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_reach_persistent launch on
+# the full BEEM-shaped workload (ncu, 1 pass; profiles/k_reach_persistent_beem-shaped.md).
+# Must be re-measured (or set to None) whenever the kernel changes.
+NCU_TRAFFIC_BYTES = {"beem": 24.16e9}
 
 
 def workload_model(name="beem"):
@@ -344,7 +348,8 @@ def main():
                    "l2": "inputs larger than L2 (4.3 GB table per step; bucket array 256 MiB)"},
         "find_or_put_ops_per_s": trans_all / (t_max / 1000.0),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (NCU_TRAFFIC_BYTES.get(args.workload) if mode == 0 else None),
                      "kernel": "k_reach_persistent" if mode == 0 else "k_reach_level",
                      "kernel_ms": kernel_ms, "algorithmic_bytes": alg, "peak_source": which},
         "random_roofline": random_roofline(got.states, got.transitions, kernel_ms, rates, peak,
