@@ -204,15 +204,18 @@ typedef struct {
 
 enum {
   REACH_PERSISTENT = 0, /* one cooperative launch runs every level (device-side level barrier) */
-  REACH_PER_LEVEL = 1   /* one launch per level; the host reads each level's size */
+  REACH_PER_LEVEL = 1,  /* one launch per level; the host reads each level's size */
+  REACH_TRACE = 4       /* flag, with REACH_PERSISTENT and the default 8-bucket line: record
+                           predecessors so that reach_ctx_deadlock_trace can print a trace */
 };
 
 typedef struct reach_ctx reach_ctx_t;
 
 /* Device bytes of a context: a table of 2^log2_buckets buckets for states of up
  * to max_state_words words, two frontier arrays of 2^log2_buckets state rows
- * (16*ceil(max_state_words/4) bytes each), a model area, counters and
- * 2*max_levels 64-bit level records. */
+ * (16*ceil(max_state_words/4) bytes each), a model area, counters,
+ * 2*max_levels 64-bit level records and three 2^log2_buckets uint32 arrays
+ * for tracing. */
 ht_status reach_ctx_bytes(int log2_buckets, int max_state_words, uint32_t max_levels,
                           uint64_t* bytes);
 ht_status reach_ctx_create(int log2_buckets, int max_state_words, uint32_t max_levels,
@@ -248,6 +251,16 @@ ht_status reach_ctx_last_timing(reach_ctx_t* c, float* kernel_ms, uint32_t* laun
  * inserted).  Synchronises `stream`; *n_levels = entries written. */
 ht_status reach_ctx_level_ns(reach_ctx_t* c, void* stream, uint64_t* level_ns_host,
                              uint32_t max_levels, uint32_t* n_levels);
+
+/* Counterexample of the last REACH_TRACE run (Alg. "Reachability analysis":
+ * a state without successors is a deadlock, "print trace"): the path from
+ * init to a deadlock of the lowest BFS level that has one, as *len state rows
+ * of state_words int32 (init first).  Which deadlock of that level, and which
+ * of several shortest paths, is the winner of the insertion races; every
+ * consecutive pair is a transition and the path has *level + 1 states.
+ * *len = 0 when the model has no deadlock.  Synchronous. */
+ht_status reach_ctx_deadlock_trace(reach_ctx_t* c, void* stream, int32_t* states_host,
+                                   uint32_t max_len, uint32_t* len, uint32_t* level);
 
 /* The context's table (owned by the context), for ht_scan / ht_gather. */
 ht_status reach_ctx_table(reach_ctx_t* c, ht_t** table);

@@ -22,7 +22,7 @@ from . import _build
 
 (HT_OK, HT_ERR_INVALID, HT_ERR_OOM, HT_ERR_FULL, HT_ERR_TIMEOUT, HT_ERR_CUDA, HT_ERR_LEVELS,
  HT_ERR_TOO_BIG) = range(8)
-REACH_PERSISTENT, REACH_PER_LEVEL = 0, 1
+REACH_PERSISTENT, REACH_PER_LEVEL, REACH_TRACE = 0, 1, 4
 STATUS_NAMES = {0: "HT_OK", 1: "HT_ERR_INVALID", 2: "HT_ERR_OOM", 3: "HT_ERR_FULL",
                 4: "HT_ERR_TIMEOUT", 5: "HT_ERR_CUDA", 6: "HT_ERR_LEVELS", 7: "HT_ERR_TOO_BIG"}
 
@@ -36,7 +36,7 @@ EXPORTED = [
     "reach_batch_bytes", "reach_batch_create", "reach_batch_create_at", "reach_batch_destroy",
     "reach_batch_run", "reach_batch_results", "reach_batch_last_timing",
     "serve_bytes", "serve_open_at", "serve_open", "serve_submit", "serve_poll", "serve_status",
-    "serve_close",
+    "serve_close", "reach_ctx_deadlock_trace",
 ]
 
 
@@ -142,6 +142,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "serve_status": [_VP, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32),
                          ctypes.POINTER(_u64), ctypes.POINTER(_u64)],
         "serve_close": [_VP],
+        "reach_ctx_deadlock_trace": [_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32),
+                                     ctypes.POINTER(ctypes.c_uint32)],
         "reach_noalloc": [ctypes.POINTER(reach_model), _VP, _i, ctypes.POINTER(ht_params), _VP, _VP,
                           ctypes.c_uint32, ctypes.POINTER(reach_result)],
         "reach": [_VP, ctypes.POINTER(reach_model), _VP, _i, _VP, _VP, ctypes.c_uint32,
@@ -515,6 +517,7 @@ class ReachContext:
 
     def load(self, model):
         _check(reach_ctx_load(self.handle, model, current_stream()), "reach_ctx_load")
+        self._W = model.state_words
 
     def run(self, mode: int = REACH_PERSISTENT):
         _check(reach_ctx_run(self.handle, mode, current_stream()), "reach_ctx_run")
@@ -528,6 +531,7 @@ class ReachContext:
 
     def reach(self, model, mode: int = REACH_PERSISTENT, raise_on_error: bool = True) -> ReachOutput:
         st, r, levels = reach(self.handle, model, mode, current_stream(), self.max_levels)
+        self._W = model.state_words
         if raise_on_error:
             _check(st, "reach")
         return ReachOutput(int(r.states), int(r.transitions), int(r.deadlocks), int(r.digest),
@@ -536,6 +540,17 @@ class ReachContext:
     def last_timing(self) -> tuple[float, int]:
         """(device ms of the last run's expansion kernels, kernels launched)."""
         return reach_ctx_last_timing(self.handle)
+
+    def deadlock_trace(self, max_len: int = 1 << 14):
+        """(level, path rows init..deadlock) of the last REACH_TRACE run, or (None, empty)."""
+        W = getattr(self, "_W", self.max_state_words)
+        buf = np.zeros((max_len, W), dtype=np.int32)
+        n, lv = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(load().reach_ctx_deadlock_trace(self.handle, current_stream(), buf.ctypes.data, max_len,
+                                               ctypes.byref(n), ctypes.byref(lv)), "reach_ctx_deadlock_trace")
+        if n.value == 0:
+            return None, buf[:0]
+        return int(lv.value), buf[:n.value]
 
     def level_ns(self) -> np.ndarray:
         """Device timestamps (ns) of the level starts of the last persistent run."""

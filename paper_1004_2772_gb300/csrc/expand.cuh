@@ -26,6 +26,20 @@ struct Acc {
   unsigned long long transitions = 0, deadlocks = 0, digest = 0, stored = 0;
 };
 
+// Counterexample support (Alg. "Reachability analysis": a state with no
+// successor is a deadlock, "print trace").  With tracing on, frontiers carry
+// each state's bucket index beside its row, every inserted state records the
+// bucket of the predecessor that inserted it, and the deadlock of the lowest
+// level (ties broken by fingerprint bits, then bucket) is kept in one word:
+//   (level << 50) | (fingerprint >> 45) << 31 | bucket.
+struct TraceDev {
+  const uint32_t* cur_idx;
+  uint32_t* next_idx;
+  uint32_t* parent;
+  unsigned long long* first_deadlock;
+  uint32_t level;
+};
+
 template <int NV>
 __device__ __forceinline__ void vec_set(Vec<NV>& v, int i, uint32_t x) {
 #pragma unroll
@@ -50,11 +64,13 @@ __device__ __forceinline__ void vec_set(Vec<NV>& v, int i, uint32_t x) {
 // New states are appended to the next frontier (rows) with one atomicAdd per
 // warp and iteration, straight from registers.
 // RT: rows have the table's run-time width t.nv (<= NV) instead of NV.
-template <int NV, int L, bool RT>
+// TR: record predecessors and the first deadlock (tr points to TraceDev).
+template <int NV, int L, bool RT, bool TR = false>
 __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m, const uint4* cur,
                                              uint32_t n_cur, uint64_t base, uint32_t spw,
                                              uint4* next, uint32_t* next_count, uint32_t cap,
-                                             Acc& acc, LocalCounters& lc, uint32_t* wsm) {
+                                             Acc& acc, LocalCounters& lc, uint32_t* wsm,
+                                             const TraceDev* tr = nullptr) {
   constexpr int RS = row_stride<NV>();
   uint32_t* rows = wsm;
   uint32_t* desc = wsm + 32 * RS;
@@ -101,6 +117,15 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
     }
     acc.transitions += c;
     if (c == 0) acc.deadlocks++;
+    if (TR) {
+      const uint32_t my = __ldcg(tr->cur_idx + f);
+      rows[lane * RS + 4 * NV + 2] = my;
+      if (c == 0) {
+        const unsigned long long key = ((unsigned long long)tr->level << 50) |
+                                       ((fingerprint(v, t.state_words) >> 45) << 31) | my;
+        atomicMin(tr->first_deadlock, key);
+      }
+    }
   }
   uint32_t incl = c;
 #pragma unroll
@@ -118,6 +143,7 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
   for (uint32_t it = 0; it < iters; ++it) {
     const uint32_t j = it * 32 + lane;
     bool is_new = false;
+    uint32_t new_idx = 0;
     Vec<NV> w;
     if (j < T) {
       uint32_t o = 0;  // owner = first lane whose inclusive prefix exceeds j
@@ -150,6 +176,10 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
         is_new = true;
         acc.digest += fingerprint(w, t.state_words);
         acc.stored++;
+        if (TR) {
+          tr->parent[sidx] = ro[4 * NV + 2];
+          new_idx = sidx;
+        }
       }
     }
     const unsigned nb = __ballot_sync(0xffffffffu, is_new);
@@ -162,6 +192,7 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
         if (pos < cap) {
           if (RT) store_row_rt<NV>(next + (size_t)pos * nvr, w, nvr);
           else store_row<NV>(next + (size_t)pos * NV, w);
+          if (TR) tr->next_idx[pos] = new_idx;
         } else {
           latch_error(t.ctr, HT_ERR_FULL);
         }

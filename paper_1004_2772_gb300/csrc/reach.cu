@@ -49,6 +49,7 @@ struct __align__(16) ReachTotals {
   uint32_t bar_pad;
   uint32_t n_levels;
   uint32_t pad;
+  unsigned long long first_deadlock;  // tracing: see TraceDev
 };
 
 struct ReachDev {
@@ -60,6 +61,9 @@ struct ReachDev {
   ReachTotals* tot;
   unsigned long long* level_sizes;
   unsigned long long* level_ns;   // globaltimer at the start of each level (persistent driver)
+  uint32_t* idx0;                 // tracing: bucket index of each frontier row
+  uint32_t* idx1;
+  uint32_t* parent;               // tracing: bucket of the predecessor that inserted a state
   uint32_t max_levels;
   uint32_t bar_spin;
 };
@@ -91,11 +95,12 @@ __device__ __forceinline__ SModel load_model_smem(const ReachDev& rd, int* sm) {
 // One level: a warp takes `spw` consecutive frontier states per round (spw
 // shrinks on small levels so that every warp gets work) and expands them with
 // expand_round.
-template <int NV, int L>
+template <int NV, int L, bool TR = false>
 __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, const uint4* cur,
                                           uint32_t n_cur, uint32_t* cursor, uint4* next,
                                           uint32_t* next_count, uint32_t cap, Acc& acc,
-                                          LocalCounters& lc, uint32_t* wsm) {
+                                          LocalCounters& lc, uint32_t* wsm,
+                                          const TraceDev* tr = nullptr) {
   const unsigned lane = lane_id();
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t warps = gridDim.x * wpb;
@@ -118,7 +123,8 @@ __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, c
       if (first) continue;
       break;
     }
-    expand_round<NV, L, false>(t, m, cur, n_cur, base, spw, next, next_count, cap, acc, lc, wsm);
+    expand_round<NV, L, false, TR>(t, m, cur, n_cur, base, spw, next, next_count, cap, acc, lc, wsm,
+                                   tr);
   }
 }
 
@@ -157,6 +163,7 @@ __device__ void seed_init(const TableView& t, const ReachDev& rd, Acc& acc, Loca
   if (r == FOP_NEW) {
 #pragma unroll
     for (int j = 0; j < NV; ++j) rd.frontier0[j] = v.c[j];
+    rd.tot->pad = idx;
     rd.tot->counts[0] = 1;
     rd.level_sizes[0] = 1;
     rd.tot->n_levels = 1;
@@ -197,7 +204,7 @@ __device__ bool grid_barrier(const ReachDev& rd, DevCounters* ctr, uint32_t& epo
   return ok != 0;
 }
 
-template <int NV, int L>
+template <int NV, int L, bool TR>
 __global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_persistent(TableView t, ReachDev rd) {
   extern __shared__ int smem[];
   const SModel m = load_model_smem(rd, smem);
@@ -208,6 +215,10 @@ __global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_persistent(TableV
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     seed_init<NV, L>(t, rd, acc, lc);
     rd.level_ns[0] = global_ns();
+    if (TR) {
+      rd.idx0[0] = rd.tot->pad;  // seed_init left init's bucket there
+      rd.parent[rd.tot->pad] = 0xFFFFFFFFu;
+    }
   }
   uint32_t epoch = 0;
   if (grid_barrier(rd, t.ctr, epoch)) {
@@ -216,8 +227,16 @@ __global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_persistent(TableV
       const uint32_t n_cur = ld_relaxed(&rd.tot->counts[k % 3]);
       const uint4* cur = (k & 1) ? rd.frontier1 : rd.frontier0;
       uint4* next = (k & 1) ? rd.frontier0 : rd.frontier1;
-      run_level<NV, L>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next,
-                       &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc, wsm);
+      TraceDev tr;
+      if (TR) {
+        tr.cur_idx = (k & 1) ? rd.idx1 : rd.idx0;
+        tr.next_idx = (k & 1) ? rd.idx0 : rd.idx1;
+        tr.parent = rd.parent;
+        tr.first_deadlock = &rd.tot->first_deadlock;
+        tr.level = k;
+      }
+      run_level<NV, L, TR>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next,
+                           &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc, wsm, &tr);
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         st_relaxed(&rd.tot->counts[(k + 2) % 3], 0u);
         st_relaxed(&rd.tot->cursor[(k + 2) % 3], 0u);
@@ -270,13 +289,16 @@ __global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_level(TableView t
 // ---------------------------------------------------------------------------
 struct ReachKernels {
   void (*persistent)(TableView, ReachDev);
+  void (*persistent_trace)(TableView, ReachDev);
   void (*seed)(TableView, ReachDev);
   void (*level)(TableView, ReachDev, uint32_t);
 };
 
 template <int NV, int L>
 static ReachKernels kernels_for() {
-  return {k_reach_persistent<NV, L>, k_reach_seed<NV, L>, k_reach_level<NV, L>};
+  // tracing is compiled for the default 8-bucket line only
+  return {k_reach_persistent<NV, L, false>, L == 8 ? k_reach_persistent<NV, 8, true> : nullptr,
+          k_reach_seed<NV, L>, k_reach_level<NV, L>};
 }
 
 template <int NV>
@@ -319,6 +341,10 @@ struct reach_ctx {
   ReachTotals* tot = nullptr;
   unsigned long long* level_sizes = nullptr;
   unsigned long long* level_ns = nullptr;
+  uint32_t* idx0 = nullptr;
+  uint32_t* idx1 = nullptr;
+  uint32_t* parent = nullptr;
+  bool traced = false;
   ReachTotals* host_tot = nullptr;     // pinned
   std::vector<int> host_blob;
   int smem_words = 0;
@@ -338,7 +364,7 @@ static uint64_t frontier_bytes(int log2_nb, int max_words) {
 static uint64_t ctx_bytes(int log2_nb, int max_words, uint32_t max_levels) {
   return align_up(table_bytes(log2_nb, max_words), 256) + align_up(kModelMaxWords * 4ull, 256) +
          2 * frontier_bytes(log2_nb, max_words) + align_up(sizeof(ReachTotals), 256) +
-         2 * align_up((uint64_t)max_levels * 8, 256);
+         2 * align_up((uint64_t)max_levels * 8, 256) + 3 * align_up((1ull << log2_nb) * 4, 256);
 }
 
 namespace vss {
@@ -431,6 +457,9 @@ static ReachDev make_rd(reach_ctx_t* c) {
   rd.tot = c->tot;
   rd.level_sizes = c->level_sizes;
   rd.level_ns = c->level_ns;
+  rd.idx0 = c->idx0;
+  rd.idx1 = c->idx1;
+  rd.parent = c->parent;
   rd.max_levels = c->max_levels;
   rd.bar_spin = 1u << 22;
   return rd;
@@ -483,6 +512,13 @@ ht_status reach_ctx_create_at(int log2_buckets, int max_state_words, uint32_t ma
   c->level_sizes = reinterpret_cast<unsigned long long*>(p);
   p += align_up((uint64_t)max_levels * 8, 256);
   c->level_ns = reinterpret_cast<unsigned long long*>(p);
+  p += align_up((uint64_t)max_levels * 8, 256);
+  const uint64_t ib = align_up((1ull << log2_buckets) * 4, 256);
+  c->idx0 = reinterpret_cast<uint32_t*>(p);
+  p += ib;
+  c->idx1 = reinterpret_cast<uint32_t*>(p);
+  p += ib;
+  c->parent = reinterpret_cast<uint32_t*>(p);
   c->log2_nb = log2_buckets;
   c->max_words = max_state_words;
   c->max_levels = max_levels;
@@ -553,6 +589,34 @@ ht_status reach_ctx_level_ns(reach_ctx_t* c, void* stream, uint64_t* level_ns_ho
   return HT_OK;
 }
 
+ht_status reach_ctx_deadlock_trace(reach_ctx_t* c, void* stream, int32_t* states_host,
+                                   uint32_t max_len, uint32_t* len, uint32_t* level) {
+  if (!c || !len || !c->traced) return HT_ERR_INVALID;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  VSS_CUDA_TRY(cudaStreamSynchronize(s));
+  unsigned long long key = 0;
+  VSS_CUDA_TRY(cudaMemcpy(&key, &c->tot->first_deadlock, 8, cudaMemcpyDeviceToHost));
+  *len = 0;
+  if (key == ~0ull) return HT_OK;  // no deadlock
+  const uint32_t lv = (uint32_t)(key >> 50);
+  if (level) *level = lv;
+  const uint32_t n = lv + 1;
+  if (!states_host || max_len < n) return HT_ERR_INVALID;
+  std::vector<uint32_t> path(n);
+  uint32_t idx = (uint32_t)(key & 0x7FFFFFFFull);
+  for (uint32_t k = n; k-- > 0;) {
+    path[k] = idx;
+    if (k) VSS_CUDA_TRY(cudaMemcpy(&idx, c->parent + idx, 4, cudaMemcpyDeviceToHost));
+  }
+  const uint32_t W = c->table.view.state_words, rw = 4 * c->table.view.nv;
+  const int32_t* data = reinterpret_cast<const int32_t*>(c->table.view.data);
+  for (uint32_t k = 0; k < n; ++k)
+    VSS_CUDA_TRY(cudaMemcpy(states_host + (uint64_t)k * W, data + (uint64_t)path[k] * rw, W * 4,
+                            cudaMemcpyDeviceToHost));
+  *len = n;
+  return HT_OK;
+}
+
 ht_status reach_ctx_table(reach_ctx_t* c, ht_t** table) {
   if (!c || !table) return HT_ERR_INVALID;
   *table = &c->table;
@@ -579,30 +643,36 @@ ht_status reach_ctx_load(reach_ctx_t* c, const reach_model* m, const int32_t* in
 
 ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
   if (!c || !c->loaded) return HT_ERR_INVALID;
+  const bool trace = (mode & REACH_TRACE) != 0;
+  mode &= ~REACH_TRACE;
   if (mode != REACH_PERSISTENT && mode != REACH_PER_LEVEL) return HT_ERR_INVALID;
+  if (trace && mode != REACH_PERSISTENT) return HT_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ht_status st = table_clear(&c->table, s);
   if (st != HT_OK) return st;
   VSS_CUDA_TRY(cudaMemsetAsync(c->tot, 0, sizeof(ReachTotals), s));
+  VSS_CUDA_TRY(cudaMemsetAsync(&c->tot->first_deadlock, 0xFF, sizeof(unsigned long long), s));
   const int threads = (int)c->table.params.block_threads;
   const size_t smem = smem_bytes_for(c, threads);
   const ReachKernels ks = pick_kernels((int)c->table.view.nv, (int)c->table.params.line_buckets);
   TableView tv = c->table.view;
   ReachDev rd = make_rd(c);
   c->last_mode = mode;
+  c->traced = trace;
   c->host_status = HT_OK;
   if (mode == REACH_PERSISTENT) {
     if (!c->coop) return HT_ERR_CUDA;
-    VSS_CUDA_TRY(cudaFuncSetAttribute(ks.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+    void (*kern)(TableView, ReachDev) = trace ? ks.persistent_trace : ks.persistent;
+    if (!kern) return HT_ERR_INVALID;  // tracing needs the default 8-bucket line
+    VSS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.persistent, threads, smem));
+    VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return HT_ERR_INVALID;
     const int blocks = per_sm * c->table.num_sms;
     void* args[] = {&tv, &rd};
     VSS_CUDA_TRY(cudaEventRecord(c->ev0, s));
-    VSS_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(ks.persistent), blocks,
-                                             threads, args, smem, s));
+    VSS_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), blocks, threads, args,
+                                             smem, s));
     VSS_CUDA_TRY(cudaEventRecord(c->ev1, s));
     c->last_launches = 1;
     return HT_OK;
@@ -800,7 +870,7 @@ extern "C" ht_status reach_noalloc(const reach_model* m, const int32_t* init_hos
   VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.persistent, threads, smem));
   if (per_sm < 1) return HT_ERR_INVALID;
   TableView tv = table.view;
-  ReachDev rd;
+  ReachDev rd{};
   rd.blob = blob;
   rd.smem_words = smem_words;
   rd.frontier0 = f0;

@@ -152,3 +152,59 @@ def test_beem_shaped_workload_full_size(cuda_lib):
     assert got.level_sizes == g["level_sizes"]
     done, writing, digest = ctx.scan()
     assert (done, writing, digest) == (g["states"], 0, int(g["digest"], 16))
+
+
+def _min_deadlock_level(m, ref):
+    """Lowest BFS level holding a state without successors (oracle states in
+    discovery order, which is level order)."""
+    r = oracle.reach(m, keep_states=True, keep_cap=1 << 21)
+    start = 0
+    for lvl, size in enumerate(ref.level_sizes):
+        if start + size > r.state_list.shape[0]:
+            return None
+        for s in r.state_list[start:start + size]:
+            if oracle.successors(m, s).shape[0] == 0:
+                return lvl
+        start += size
+    return None
+
+
+def _check_trace(m, level, path, ref):
+    assert level == _min_deadlock_level(m, ref)
+    assert path.shape[0] == level + 1
+    assert np.array_equal(path[0], m.init)
+    for a, b in zip(path[:-1], path[1:]):
+        succ = oracle.successors(m, a)
+        assert any(np.array_equal(b, x) for x in succ), "consecutive trace states are not a transition"
+    assert oracle.successors(m, path[-1]).shape[0] == 0
+
+
+@pytest.mark.parametrize("which", ["deadlock-chain", "tiny0", "tiny1", "tiny2", "medium"])
+def test_deadlock_trace(cuda_lib, which):
+    if which == "deadlock-chain":
+        m = [m for m, d in hand_models() if d["name"] == which][0]
+        lg = 8
+    elif which == "medium":
+        g = load_golden("beem_medium.json")
+        m = synth.beem_shaped_model(**g["model"])
+        lg = g["log2_buckets"]
+    else:
+        kws = [kw for kw in TINY_BEEM if oracle.reach(synth.beem_shaped_model(**kw)).deadlocks > 0]
+        m = synth.beem_shaped_model(**kws[int(which[-1])])
+        lg = 12
+    ref = oracle.reach(m)
+    assert ref.deadlocks > 0
+    ctx = cuda_lib.ReachContext(lg, m.state_words, max_levels=4096)
+    got = ctx.reach(m, mode=cuda_lib.REACH_PERSISTENT | cuda_lib.REACH_TRACE)
+    assert (got.states, got.transitions, got.deadlocks, got.digest, got.level_sizes) == (
+        ref.states, ref.transitions, ref.deadlocks, ref.digest, ref.level_sizes)
+    level, path = ctx.deadlock_trace()
+    _check_trace(m, level, path, ref)
+
+
+def test_no_deadlock_no_trace(cuda_lib):
+    m = synth.tiny_interleaving_model()
+    ctx = cuda_lib.ReachContext(18, 5, max_levels=256)
+    ctx.reach(m, mode=cuda_lib.REACH_PERSISTENT | cuda_lib.REACH_TRACE)
+    level, path = ctx.deadlock_trace()
+    assert level is None and path.shape[0] == 0
