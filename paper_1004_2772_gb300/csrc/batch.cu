@@ -416,8 +416,10 @@ __global__ void __launch_bounds__(256, 2) k_reach_batch(BatchGlobal g) {
       expand_round<kBatchNV, L, true>(t, sm, ldm(M.fr[cur]), ldm(M.n_cur), u0, cnt,
                                       ldm(M.fr[cur ^ 1u]), &M.next_count[e & 1u],
                                       (uint32_t)(1ull << lg), acc, lc, wsm);
-      const unsigned long long tr = warp_sum(acc.transitions), dl = warp_sum(acc.deadlocks);
-      const unsigned long long dg = warp_sum(acc.digest), st = warp_sum(acc.stored);
+      const unsigned long long tr = warp_sum((unsigned long long)acc.transitions);
+      const unsigned long long dl = warp_sum((unsigned long long)acc.deadlocks);
+      const unsigned long long dg = warp_sum(acc.digest);
+      const unsigned long long st = warp_sum((unsigned long long)acc.stored);
       const uint32_t bw = warp_sum(lc.busy_waits), rh = warp_sum(lc.rehashes);
       if (lane == 0) {
         if (tr) atomicAdd(&M.transitions, tr);

@@ -6,7 +6,14 @@
 
 namespace vss {
 
-constexpr int kDescCap = 1024;  // successor descriptors per warp and round
+#ifndef VSS_DESC_CAP
+#define VSS_DESC_CAP 1024
+#endif
+constexpr int kDescCap = VSS_DESC_CAP;  // successor descriptors per warp and round
+
+#ifndef VSS_WARP_DEDUP
+#define VSS_WARP_DEDUP 0  // merge equal successors of one warp iteration before probing
+#endif
 
 template <int NV>
 __host__ __device__ constexpr int row_stride() { return 4 * NV + 4; }  // padded: conflict-free 16 B reads
@@ -22,8 +29,11 @@ struct SModel {
   const int* uval;
 };
 
+// Per-thread counters (a thread sees far fewer than 2^32 transitions between
+// flushes); the digest needs all 64 bits.
 struct Acc {
-  unsigned long long transitions = 0, deadlocks = 0, digest = 0, stored = 0;
+  uint32_t transitions = 0, deadlocks = 0, stored = 0;
+  unsigned long long digest = 0;
 };
 
 // Counterexample support (Alg. "Reachability analysis": a state with no
@@ -145,7 +155,10 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
     bool is_new = false;
     uint32_t new_idx = 0;
     Vec<NV> w;
-    if (j < T) {
+    const bool valid = j < T;
+    uint64_t h = 0;
+    uint32_t parent_idx = 0;
+    if (valid) {
       uint32_t o = 0;  // owner = first lane whose inclusive prefix exceeds j
 #pragma unroll
       for (uint32_t step = 16; step > 0; step >>= 1)
@@ -169,17 +182,52 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
         hs += hash_term(t.seed, q, uv) - hash_term(t.seed, q, ro[q]);
         vec_set(w, q, uv);
       }
-      const uint64_t h = hash_final(hs, t.state_words);
-      uint32_t sidx = 0;
-      const int res = find_or_put<NV, L, RT>(t, w, h, sidx, lc);
-      if (res == FOP_NEW) {
-        is_new = true;
-        acc.digest += fingerprint(w, t.state_words);
-        acc.stored++;
-        if (TR) {
-          tr->parent[sidx] = ro[4 * NV + 2];
-          new_idx = sidx;
+      h = hash_final(hs, t.state_words);
+      if (TR) parent_idx = ro[4 * NV + 2];
+    }
+    // Siblings share successors (diamonds), so equal successors often meet in
+    // one iteration: the lowest such lane probes, the others confirm equality
+    // word by word and take its answer as "seen" instead of waiting on a
+    // bucket in the write state.
+    bool probe = valid;
+    int lead = (int)lane;
+#if VSS_WARP_DEDUP
+    {
+      const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+      const unsigned grp = __match_any_sync(0xffffffffu, h) & vmask;
+      if (__any_sync(0xffffffffu, valid && __popc(grp) > 1)) {
+        const int ld = valid ? __ffs(grp) - 1 : (int)lane;
+        uint32_t diff = 0;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          diff |= __shfl_sync(0xffffffffu, w.c[q].x, ld) ^ w.c[q].x;
+          diff |= __shfl_sync(0xffffffffu, w.c[q].y, ld) ^ w.c[q].y;
+          diff |= __shfl_sync(0xffffffffu, w.c[q].z, ld) ^ w.c[q].z;
+          diff |= __shfl_sync(0xffffffffu, w.c[q].w, ld) ^ w.c[q].w;
         }
+        if (valid && ld != (int)lane && diff == 0) {
+          probe = false;
+          lead = ld;
+        }
+      }
+    }
+#endif
+    int res = FOP_SEEN;
+    uint32_t sidx = 0;
+    if (probe) res = find_or_put<NV, L, RT>(t, w, h, sidx, lc);
+#if VSS_WARP_DEDUP
+    {
+      const int lres = __shfl_sync(0xffffffffu, res, lead);
+      if (valid && !probe && lres == FOP_ERR) res = FOP_ERR;
+    }
+#endif
+    if (valid && res == FOP_NEW) {
+      is_new = true;
+      acc.digest += fingerprint(w, t.state_words);
+      acc.stored++;
+      if (TR) {
+        tr->parent[sidx] = parent_idx;
+        new_idx = sidx;
       }
     }
     const unsigned nb = __ballot_sync(0xffffffffu, is_new);

@@ -25,6 +25,12 @@
 
 namespace vss {
 
+#ifndef VSS_ROUNDS_PER_WARP
+#define VSS_ROUNDS_PER_WARP 1  // target rounds per warp and level (more measured slower)
+#endif
+#ifndef VSS_BARRIER_STATS
+#define VSS_BARRIER_STATS 0  // measurement builds only: record barrier arrival spreads
+#endif
 #ifndef VSS_REACH_MINB
 #define VSS_REACH_MINB 3  // __launch_bounds__ minimum resident blocks of the expansion kernels
 #endif             // successor descriptors per warp and round
@@ -104,7 +110,10 @@ __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, c
   const unsigned lane = lane_id();
   const uint32_t wpb = blockDim.x >> 5;
   const uint32_t warps = gridDim.x * wpb;
-  uint32_t spw = (n_cur + warps - 1) / warps;
+  // aim for several rounds per warp so that the dynamic claims balance the
+  // level's end (a single static round leaves the level to its slowest warp)
+  const uint32_t per = warps * (uint32_t)VSS_ROUNDS_PER_WARP;
+  uint32_t spw = (n_cur + per - 1) / per;
   spw = spw < 1u ? 1u : (spw > (uint32_t)m.spw_max ? (uint32_t)m.spw_max : spw);
   const uint32_t warp_id = blockIdx.x * wpb + (threadIdx.x >> 5);
   const uint64_t static_rows = (uint64_t)warps * spw;
@@ -130,10 +139,10 @@ __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, c
 
 __device__ __forceinline__ void flush_acc(const TableView& t, const ReachDev& rd, Acc& acc,
                                           LocalCounters& lc) {
-  const unsigned long long tr = warp_sum(acc.transitions);
-  const unsigned long long dl = warp_sum(acc.deadlocks);
+  const unsigned long long tr = warp_sum((unsigned long long)acc.transitions);
+  const unsigned long long dl = warp_sum((unsigned long long)acc.deadlocks);
   const unsigned long long dg = warp_sum(acc.digest);
-  const unsigned long long st = warp_sum(acc.stored);
+  const unsigned long long st = warp_sum((unsigned long long)acc.stored);
   const uint32_t bw = warp_sum(lc.busy_waits);
   const uint32_t rh = warp_sum(lc.rehashes);
   if (lane_id() == 0) {
@@ -188,6 +197,14 @@ __device__ bool grid_barrier(const ReachDev& rd, DevCounters* ctr, uint32_t& epo
   ++epoch;
   if (threadIdx.x == 0) {
     int good = 1;
+#if VSS_BARRIER_STATS
+    // measurement build: first and last block arrival of every barrier
+    if (epoch < rd.max_levels) {
+      const unsigned long long now = global_ns();
+      atomicMin(&rd.level_ns[rd.max_levels / 2 + epoch], now);
+      atomicMax(&rd.level_sizes[rd.max_levels / 2 + epoch], now);
+    }
+#endif
     const uint32_t target = epoch * gridDim.x;
     asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&rd.tot->bar_count) : "memory");
     uint32_t spins = 0, ns = 32;

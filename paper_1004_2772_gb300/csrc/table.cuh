@@ -110,43 +110,49 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
       line = (line + step) & t.lines_mask;
     }
     const uint32_t line_base = line * L;
-    uint32_t first[8];  // words of sector s0, kept for the wrap-around part of the walk
+    // A sector is kept as three 8-bit masks (empty / memo-equal / done), not
+    // as its eight words: the walk only ever acts on empty or memo-equal
+    // buckets, whose words the masks determine.  f_* hold sector s0 for the
+    // wrap-around part of the walk (a longer line visits it twice).
+    uint32_t f_emp = 0, f_mem = 0, f_dn = 0;
 #pragma unroll 1
     for (int v = 0; v <= NS; ++v) {
       const uint32_t sec = (s0 + (uint32_t)v) & (NS - 1);
       const uint32_t base = line_base + sec * 8;
-      uint32_t w[8];
-      if (v == 0 || v == NS) {
-        if (v == 0) {
-          uint4 a, b;
-          ld_sector(t.buckets + base, a, b);
-          first[0] = a.x; first[1] = a.y; first[2] = a.z; first[3] = a.w;
-          first[4] = b.x; first[5] = b.y; first[6] = b.z; first[7] = b.w;
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k) w[k] = first[k];
-      } else {
+      uint32_t emp, mem, dn;
+      if (v == 0 || v != NS) {
         uint4 a, b;
         ld_sector(t.buckets + base, a, b);
-        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
-        w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+        const uint32_t wd[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        emp = 0;
+        mem = 0;
+        dn = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          emp |= (wd[k] == 0u ? 1u : 0u) << k;
+          mem |= ((wd[k] & kMemoMask) == memo ? 1u : 0u) << k;
+          dn |= (wd[k] >> 31) << k;
+        }
+        if (v == 0) {
+          f_emp = emp;
+          f_mem = mem;
+          f_dn = dn;
+        }
+      } else {
+        emp = f_emp;
+        mem = f_mem;
+        dn = f_dn;
       }
       // positions of this visit, in walk order = ascending inside the sector
       uint32_t todo = (v == 0) ? (0xFFu << p0) & 0xFFu : (v == NS) ? (1u << p0) - 1u : 0xFFu;
       while (todo) {
-        uint32_t cand = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-          cand |= ((w[k] == 0u) | ((w[k] & kMemoMask) == memo) ? 1u : 0u) << k;
-        cand &= todo;
+        const uint32_t cand = (emp | mem) & todo;
         if (!cand) break;
         const int pos = __ffs(cand) - 1;
+        const uint32_t bit = 1u << pos;
         const uint32_t i = base + pos;
-        uint32_t b = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) b = (k == pos) ? w[k] : b;
         bool acquired = (VSS_ACQ_MODE == 1);  // sector words came from acquire loads
-        if (b == 0u) {
+        if (emp & bit) {
           const uint32_t old = atomicCAS(t.buckets + i, 0u, memo);  // <memo, write>
           if (old == 0u) {
             if (RT) store_row_rt<NV>(t.data + (size_t)i * t.nv, key, t.nv);
@@ -156,12 +162,14 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
             out_idx = i;
             return FOP_NEW;
           }
-          b = old;
+          // another thread claimed it first: re-evaluate with the word it wrote
           acquired = false;  // a relaxed CAS result: fence before reading the row
-#pragma unroll
-          for (int k = 0; k < 8; ++k) w[k] = (k == pos) ? old : w[k];
+          emp &= ~bit;
+          mem = ((old & kMemoMask) == memo) ? (mem | bit) : (mem & ~bit);
+          dn = (old & kDone) ? (dn | bit) : (dn & ~bit);
         }
-        if ((b & kMemoMask) == memo) {
+        if (mem & bit) {
+          uint32_t b = memo | ((dn & bit) ? kDone : 0u);
           if (!(b & kDone)) {
             if (!wait_done(t, i, b, lc)) return FOP_ERR;
             acquired = true;
