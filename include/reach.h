@@ -58,15 +58,29 @@ enum {
 #define HT_BUCKET_DONE 0x80000000u
 #define HT_BUCKET_MEMO 0x7FFFFFFFu
 
+/* Narrow bucket layout, selected by ht_params.bucket_bits = 16 (Section 1 names
+ * the bucket size among the parameters left to the implementation):
+ *   0            empty
+ *   bit 15       write / done, as above
+ *   bits 0..14   memo = bits 49..63 of the state hash, 0 mapped to 1.
+ * Half the bytes per bucket, so twice as many buckets share one 32-byte sector
+ * and the bucket array is half as large; a shorter memo lets more foreign keys
+ * through to a data compare (about 1 in 2^15 per memo-bucket visited). */
+#define HT_BUCKET16_DONE 0x8000u
+#define HT_BUCKET16_MEMO 0x7FFFu
+
 /* Tunable layout and safety limits; 0 in any field selects the default. */
 typedef struct {
-  uint32_t line_buckets;  /* buckets walked per line before rehashing: 8, 16 or 32
-                             (32, 64 or 128 bytes); default 8 */
+  uint32_t line_buckets;  /* buckets walked per line before rehashing.  32-bit buckets:
+                             8, 16 or 32 (32, 64 or 128 bytes), default 8; 16-bit
+                             buckets: 16 or 32 (32 or 64 bytes), default 16 */
   uint32_t max_rehash;    /* lines probed before HT_ERR_FULL; default min(lines, 4096) */
   uint32_t max_spin;      /* polls of a write-busy bucket before HT_ERR_TIMEOUT; default 2^18 */
   uint32_t block_threads; /* threads per block of the batch and expansion kernels; default 256 */
   uint32_t dedup;         /* 1 = merge equal keys inside a warp before probing (batch API) */
-  uint32_t reserved;
+  uint32_t bucket_bits;   /* bucket word width: 32 (default) or 16 (the layouts above).
+                             ht_scan, ht_arrays and reach_* follow it; the batch
+                             and serving entry points accept only 32 */
   uint64_t hash_seed;     /* seed of the table hash; default a fixed constant */
 } ht_params;
 
@@ -77,8 +91,9 @@ typedef struct {
 typedef struct ht ht_t;
 
 /* Device bytes needed by a table of 2^log2_buckets buckets for state vectors of
- * state_words int32 words: 4 bytes per bucket, 16*ceil(state_words/4) bytes of
- * data per bucket (rows padded to 16 bytes), plus a small header. */
+ * state_words int32 words: 4 bytes per bucket (enough for either bucket width),
+ * 16*ceil(state_words/4) bytes of data per bucket (rows padded to 16 bytes),
+ * plus a small header. */
 ht_status ht_bytes(int log2_buckets, int state_words, uint64_t* bytes);
 
 /* Create an empty table (Section 3.1: no allocation during operation; the
@@ -131,8 +146,9 @@ ht_status ht_scan(ht_t* h, void* stream, uint64_t* done, uint64_t* writing, uint
 /* Copy rows idx_dev[0..n) of the data array to out_dev (n x state_words int32). */
 ht_status ht_gather(ht_t* h, const uint32_t* idx_dev, uint64_t n, int32_t* out_dev, void* stream);
 
-/* Device pointers to the bucket array (uint32[2^log2_buckets]) and data array
- * (rows of 4*ceil(state_words/4) int32), for inspection. */
+/* Device pointers to the bucket array (2^log2_buckets words of bucket_bits
+ * bits: uint32 or uint16) and data array (rows of 4*ceil(state_words/4) int32),
+ * for inspection. */
 ht_status ht_arrays(ht_t* h, uint32_t** buckets_dev, int32_t** data_dev, uint32_t* row_words);
 
 /* ------------------------------------------------------------------------ */
@@ -400,6 +416,9 @@ ht_status reach_noalloc(const reach_model* m, const int32_t* init_host, int log2
  * bytes (256-byte aligned; its contents are overwritten), unit by mode:
  *   0  read one 32-byte sector          1  read 64 bytes (two adjacent sectors)
  *   2  write one 32-byte sector         3  32-bit atomicAdd (a sector RMW in L2)
+ *   4  32-bit compare-and-swap          5  16-bit compare-and-swap
+ *   6  32-bit relaxed store             7  16-bit relaxed store
+ * (4..7 are the claim and publish steps of an insert for either bucket width.)
  * Every thread keeps 8 accesses in flight.  *ms = device time from CUDA events
  * on `stream`.  Synchronous.  Use a buffer much larger than L2 (e.g. 16 GiB). */
 ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_access, int mode, void* stream,

@@ -6,6 +6,8 @@ the tunable ones are
 
     line_buckets   buckets walked per line before rehashing (8, 16, 32: a 32-,
                    64- or 128-byte line, read one 32-byte sector at a time)
+    bucket_bits    bucket width: 32 (31-bit memo) or 16 (15-bit memo, half the
+                   bucket array, lines of 16 or 32 buckets)
     dedup          merge equal keys inside a warp before probing (hot keys)
     block_threads  threads per block of the batch / expansion kernels
     log2_buckets   table size for a given number of keys (the load factor)
@@ -14,8 +16,7 @@ Every candidate must give identical results (number of keys stored and the
 digest of the stored set for the key-stream benchmark; states, transitions,
 level sizes and digest for reachability); a candidate that disagrees is an
 error, not a slower choice.  Choices are cached in a JSON file keyed by the
-workload shape.  Bucket width (32-bit words: a 31-bit memo and the write
-bit) and the hash family are fixed by the implementation.
+workload shape.  The hash family is fixed by the implementation.
 """
 from __future__ import annotations
 
@@ -30,8 +31,12 @@ from . import binding as B
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1004_2772_gb300_autotune.json")
 
-TABLE_SPACE = {"line_buckets": (8, 16, 32), "dedup": (0, 1), "block_threads": (128, 256)}
-REACH_SPACE = {"line_buckets": (8, 16, 32), "block_threads": (128, 256)}
+TABLE_SPACE = {"line_buckets": (8, 16, 32), "bucket_bits": (32, 16), "dedup": (0, 1),
+               "block_threads": (128, 256)}
+REACH_SPACE = {"line_buckets": (8, 16, 32), "bucket_bits": (32, 16), "block_threads": (128, 256)}
+
+# line lengths each bucket width supports (a line is 1, 2 or 4 sectors of 32 bytes)
+LINES_FOR_WIDTH = {32: (8, 16, 32), 16: (16, 32)}
 
 
 def _load_cache(path):
@@ -53,7 +58,10 @@ def _save_cache(path, cache):
 def _candidates(space):
     keys = sorted(space)
     for vals in itertools.product(*(space[k] for k in keys)):
-        yield dict(zip(keys, vals))
+        cand = dict(zip(keys, vals))
+        if cand.get("line_buckets", 0) not in LINES_FOR_WIDTH[cand.get("bucket_bits", 32)] + (0,):
+            continue
+        yield cand
 
 
 def time_fill(tab, seed, n_ids, zipf=None, reps=1):

@@ -49,7 +49,7 @@ class HtError(RuntimeError):
 class ht_params(ctypes.Structure):
     _fields_ = [("line_buckets", ctypes.c_uint32), ("max_rehash", ctypes.c_uint32),
                 ("max_spin", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("dedup", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("dedup", ctypes.c_uint32), ("bucket_bits", ctypes.c_uint32),
                 ("hash_seed", ctypes.c_uint64)]
 
 
@@ -326,17 +326,19 @@ def vss_probe_random(buf_dev: int, nbytes: int, n_access: int, mode: int, stream
     return ms.value
 
 
-PROBE_MODES = {0: "read 32 B", 1: "read 64 B", 2: "write 32 B", 3: "atomic 32-bit"}
+PROBE_MODES = {0: "read 32 B", 1: "read 64 B", 2: "write 32 B", 3: "atomic 32-bit",
+               4: "CAS 32-bit", 5: "CAS 16-bit", 6: "store 32-bit", 7: "store 16-bit"}
 
 
-def random_access_rates(gib: int = 16, n_access: int = 1 << 28, device="cuda") -> dict:
-    """Random accesses per second for each probe mode over a `gib` GiB buffer."""
+def random_access_rates(gib: float = 16, n_access: int = 1 << 28, device="cuda",
+                        modes=(0, 1, 2, 3)) -> dict:
+    """Random accesses per second for the given probe modes over a `gib` GiB buffer."""
     torch = _torch()
-    nbytes = gib << 30
+    nbytes = int(gib * (1 << 30)) // 256 * 256
     buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
     ptr = (buf.data_ptr() + 255) // 256 * 256
     out = {}
-    for mode in PROBE_MODES:
+    for mode in modes:
         vss_probe_random(ptr, nbytes, n_access // 8, mode, current_stream())  # warm-up
         ms = min(vss_probe_random(ptr, nbytes, n_access, mode, current_stream()) for _ in range(3))
         out[mode] = n_access / (ms / 1e3)
@@ -468,12 +470,16 @@ class Table:
         return out
 
     def arrays(self):
-        """(buckets uint32 view as int32 tensor, data int32 tensor [nb, row_words])."""
+        """(bucket words as an int32 tensor, or int16 for 16-bit buckets; data
+        int32 tensor [nb, row_words])."""
         torch = _torch()
         b, d, rw = ht_arrays(self.handle)
         nb = 1 << self.log2_buckets
         base = self.mem.data_ptr()
-        buckets = self.mem[b - base:b - base + 4 * nb].view(torch.int32)
+        if self.params.bucket_bits == 16:
+            buckets = self.mem[b - base:b - base + 2 * nb].view(torch.int16)
+        else:
+            buckets = self.mem[b - base:b - base + 4 * nb].view(torch.int32)
         data = self.mem[d - base:d - base + 4 * nb * rw].view(torch.int32).view(nb, rw)
         return buckets, data
 

@@ -87,6 +87,7 @@ __device__ __forceinline__ TableView model_table(const BatchModel& M, const Batc
   t.max_spin = g.max_spin;
   t.state_words = M.W;
   t.nv = M.nv;
+  t.bucket_bits = 32;
   return t;
 }
 
@@ -564,6 +565,7 @@ ht_status reach_batch_create_at(const reach_model* models, const int32_t* const*
   ht_params p{};
   st = resolve_params(params, 10, &p);
   if (st != HT_OK) return st;
+  if (p.bucket_bits != 32) return HT_ERR_INVALID;  // batch tables use 32-bit buckets
   reach_batch_t* b = new (std::nothrow) reach_batch_t();
   if (!b) return HT_ERR_OOM;
   b->n_models = n_models;

@@ -75,7 +75,7 @@ __device__ __forceinline__ void vec_set(Vec<NV>& v, int i, uint32_t x) {
 // warp and iteration, straight from registers.
 // RT: rows have the table's run-time width t.nv (<= NV) instead of NV.
 // TR: record predecessors and the first deadlock (tr points to TraceDev).
-template <int NV, int L, bool RT, bool TR = false>
+template <int NV, int L, bool RT, bool TR = false, int BW = 32>
 __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m, const uint4* cur,
                                              uint32_t n_cur, uint64_t base, uint32_t spw,
                                              uint4* next, uint32_t* next_count, uint32_t cap,
@@ -96,7 +96,7 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
     uint4* r = reinterpret_cast<uint4*>(rows + lane * RS);
     Vec<NV> v;
     if (RT) load_row_cg_rt<NV>(cur + f * nvr, v, nvr);
-    else load_row_cg<NV>(cur + f * NV, v);
+    else load_front<NV>(cur + f * NV, v);
 #pragma unroll
     for (int j = 0; j < NV; ++j) r[j] = v.c[j];
     // the parent's hash sum, kept in the row's padding for its successors
@@ -190,8 +190,8 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
     // word by word and take its answer as "seen" instead of waiting on a
     // bucket in the write state.
     bool probe = valid;
-    int lead = (int)lane;
 #if VSS_WARP_DEDUP
+    int lead = (int)lane;
     {
       const unsigned vmask = __ballot_sync(0xffffffffu, valid);
       const unsigned grp = __match_any_sync(0xffffffffu, h) & vmask;
@@ -214,7 +214,7 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
 #endif
     int res = FOP_SEEN;
     uint32_t sidx = 0;
-    if (probe) res = find_or_put<NV, L, RT>(t, w, h, sidx, lc);
+    if (probe) res = find_or_put<NV, L, RT, BW>(t, w, h, sidx, lc);
 #if VSS_WARP_DEDUP
     {
       const int lres = __shfl_sync(0xffffffffu, res, lead);
@@ -239,7 +239,7 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
         const uint32_t pos = wbase + __popc(nb & ((1u << lane) - 1u));
         if (pos < cap) {
           if (RT) store_row_rt<NV>(next + (size_t)pos * nvr, w, nvr);
-          else store_row<NV>(next + (size_t)pos * NV, w);
+          else store_front<NV>(next + (size_t)pos * NV, w);
           if (TR) tr->next_idx[pos] = new_idx;
         } else {
           latch_error(t.ctr, HT_ERR_FULL);

@@ -21,7 +21,10 @@ __device__ __forceinline__ uint64_t probe_mix(uint64_t z) {
 }
 
 // mode 0: read one 32 B sector; 1: read 64 B (two adjacent sectors, 64 B
-// aligned); 2: write one 32 B sector; 3: atomicAdd on one 32-bit word.
+// aligned); 2: write one 32 B sector; 3: atomicAdd on one 32-bit word;
+// 4 / 5: compare-and-swap (0 -> x) on a 32- / 16-bit word; 6 / 7: relaxed
+// gpu-scope store of one 32- / 16-bit word (the claim and publish steps of an
+// insert, for either bucket width).
 template <int MODE>
 __global__ void __launch_bounds__(256) k_probe(uint4* buf, uint64_t n_units, uint64_t n_access,
                                                uint64_t seed, unsigned long long* sink) {
@@ -52,10 +55,30 @@ __global__ void __launch_bounds__(256) k_probe(uint4* buf, uint64_t n_units, uin
           st_v8(buf + u[k] * 2, w, w);
         }
       }
-    } else {
+    } else if (MODE == 3) {
 #pragma unroll
       for (int k = 0; k < kInflight; ++k)
         if (base + k < n_access) atomicAdd(reinterpret_cast<uint32_t*>(buf + u[k] * 2), 1u);
+    } else if (MODE == 4) {
+#pragma unroll
+      for (int k = 0; k < kInflight; ++k)
+        if (base + k < n_access)
+          acc ^= atomicCAS(reinterpret_cast<uint32_t*>(buf + u[k] * 2), 0u, (uint32_t)u[k] | 1u);
+    } else if (MODE == 5) {
+#pragma unroll
+      for (int k = 0; k < kInflight; ++k)
+        if (base + k < n_access)
+          acc ^= atomicCAS(reinterpret_cast<unsigned short*>(buf + u[k] * 2), (unsigned short)0,
+                           (unsigned short)(u[k] | 1u));
+    } else if (MODE == 6) {
+#pragma unroll
+      for (int k = 0; k < kInflight; ++k)
+        if (base + k < n_access) st_relaxed(reinterpret_cast<uint32_t*>(buf + u[k] * 2), (uint32_t)k);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kInflight; ++k)
+        if (base + k < n_access)
+          st_relaxed_u16(reinterpret_cast<uint16_t*>(buf + u[k] * 2), (uint32_t)k);
     }
   }
   if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);  // keeps the loads alive
@@ -67,7 +90,7 @@ using namespace vss;
 
 extern "C" ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_access, int mode,
                                       void* stream, float* ms) {
-  if (!buf_dev || !ms || mode < 0 || mode > 3 || (reinterpret_cast<uintptr_t>(buf_dev) & 255u))
+  if (!buf_dev || !ms || mode < 0 || mode > 7 || (reinterpret_cast<uintptr_t>(buf_dev) & 255u))
     return HT_ERR_INVALID;
   const uint64_t unit = (mode == 1) ? 64 : 32;
   const uint64_t n_units = bytes / unit;
@@ -90,7 +113,11 @@ extern "C" ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_
     case 0: k_probe<0><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
     case 1: k_probe<1><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
     case 2: k_probe<2><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
-    default: k_probe<3><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
+    case 3: k_probe<3><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
+    case 4: k_probe<4><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
+    case 5: k_probe<5><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
+    case 6: k_probe<6><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
+    default: k_probe<7><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
   }
   VSS_CUDA_TRY(cudaGetLastError());
   VSS_CUDA_TRY(cudaEventRecord(e1, s));

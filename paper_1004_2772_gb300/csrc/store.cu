@@ -12,7 +12,7 @@ namespace vss {
 // the lowest such lane probes, the others compare their key with it through
 // shuffles and take its answer as "seen" -- this removes write-busy waits on
 // hot keys that arrive together.
-template <int NV, int L, bool DEDUP>
+template <int NV, int L, bool DEDUP, int BW>
 __global__ void __launch_bounds__(256) k_find_or_put(TableView t, const int32_t* __restrict__ keys,
                                                      uint64_t n, uint8_t* __restrict__ seen,
                                                      uint32_t* __restrict__ idx) {
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(256) k_find_or_put(TableView t, const int32_t*
         }
       }
     }
-    if (probe) res = find_or_put<NV, L>(t, key, h, out, lc);
+    if (probe) res = find_or_put<NV, L, false, BW>(t, key, h, out, lc);
     if (DEDUP) {
       const int lres = __shfl_sync(0xffffffffu, res, leader);
       const uint32_t lout = __shfl_sync(0xffffffffu, out, leader);
@@ -94,8 +94,9 @@ __global__ void __launch_bounds__(256) k_scan(TableView t, uint64_t nb, unsigned
   unsigned long long done = 0, writing = 0, dig = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t b = ld_relaxed(t.buckets + i);
-    if (b & kDone) {
+    const uint32_t b = t.bucket_bits == 16 ? Bucket<16>::load_relaxed(t.buckets, i)
+                                           : Bucket<32>::load_relaxed(t.buckets, i);
+    if (b & (t.bucket_bits == 16 ? Bucket<16>::kDoneBit : Bucket<32>::kDoneBit)) {
       Vec<NV> row;
       load_row<NV>(t.data + i * NV, row);
       dig += fingerprint(row, t.state_words);
@@ -131,25 +132,31 @@ __global__ void k_gather(TableView t, const uint32_t* __restrict__ idx, uint64_t
 // ---------------------------------------------------------------------------
 using FopKernel = void (*)(TableView, const int32_t*, uint64_t, uint8_t*, uint32_t*);
 
+template <int NV, int L, int BW>
+static FopKernel pick_fop_l(bool dedup) {
+  return dedup ? k_find_or_put<NV, L, true, BW> : k_find_or_put<NV, L, false, BW>;
+}
+
 template <int NV>
-static FopKernel pick_fop_nv(int L, bool dedup) {
+static FopKernel pick_fop_nv(int L, int bw, bool dedup) {
+  if (bw == 16) return L == 16 ? pick_fop_l<NV, 16, 16>(dedup) : pick_fop_l<NV, 32, 16>(dedup);
   switch (L) {
-    case 8: return dedup ? k_find_or_put<NV, 8, true> : k_find_or_put<NV, 8, false>;
-    case 16: return dedup ? k_find_or_put<NV, 16, true> : k_find_or_put<NV, 16, false>;
-    default: return dedup ? k_find_or_put<NV, 32, true> : k_find_or_put<NV, 32, false>;
+    case 8: return pick_fop_l<NV, 8, 32>(dedup);
+    case 16: return pick_fop_l<NV, 16, 32>(dedup);
+    default: return pick_fop_l<NV, 32, 32>(dedup);
   }
 }
 
-static FopKernel pick_fop(int nv, int L, bool dedup) {
+static FopKernel pick_fop(int nv, int L, int bw, bool dedup) {
   switch (nv) {
-    case 1: return pick_fop_nv<1>(L, dedup);
-    case 2: return pick_fop_nv<2>(L, dedup);
-    case 3: return pick_fop_nv<3>(L, dedup);
-    case 4: return pick_fop_nv<4>(L, dedup);
-    case 5: return pick_fop_nv<5>(L, dedup);
-    case 6: return pick_fop_nv<6>(L, dedup);
-    case 7: return pick_fop_nv<7>(L, dedup);
-    default: return pick_fop_nv<8>(L, dedup);
+    case 1: return pick_fop_nv<1>(L, bw, dedup);
+    case 2: return pick_fop_nv<2>(L, bw, dedup);
+    case 3: return pick_fop_nv<3>(L, bw, dedup);
+    case 4: return pick_fop_nv<4>(L, bw, dedup);
+    case 5: return pick_fop_nv<5>(L, bw, dedup);
+    case 6: return pick_fop_nv<6>(L, bw, dedup);
+    case 7: return pick_fop_nv<7>(L, bw, dedup);
+    default: return pick_fop_nv<8>(L, bw, dedup);
   }
 }
 
@@ -182,8 +189,16 @@ uint64_t table_bytes(int log2_nb, int max_words) {
 ht_status resolve_params(const ht_params* in, int log2_nb, ht_params* out) {
   ht_params p{};
   if (in) p = *in;
-  if (p.line_buckets == 0) p.line_buckets = 8;
-  if (p.line_buckets != 8 && p.line_buckets != 16 && p.line_buckets != 32) return HT_ERR_INVALID;
+  if (p.bucket_bits == 0) p.bucket_bits = 32;
+  if (p.bucket_bits == 32) {
+    if (p.line_buckets == 0) p.line_buckets = 8;
+    if (p.line_buckets != 8 && p.line_buckets != 16 && p.line_buckets != 32) return HT_ERR_INVALID;
+  } else if (p.bucket_bits == 16) {
+    if (p.line_buckets == 0) p.line_buckets = 16;
+    if (p.line_buckets != 16 && p.line_buckets != 32) return HT_ERR_INVALID;
+  } else {
+    return HT_ERR_INVALID;
+  }
   if ((1ull << log2_nb) < p.line_buckets) return HT_ERR_INVALID;
   const uint64_t lines = (1ull << log2_nb) / p.line_buckets;
   if (p.max_rehash == 0) p.max_rehash = (uint32_t)(lines < 4096 ? lines : 4096);
@@ -219,6 +234,7 @@ ht_status table_init_at(ht_t* h, int log2_nb, int max_words, const ht_params* pa
   h->view.max_spin = h->params.max_spin;
   h->view.state_words = (uint32_t)max_words;
   h->view.nv = (uint32_t)nv;
+  h->view.bucket_bits = h->params.bucket_bits;
   h->log2_nb = log2_nb;
   h->max_words = max_words;
   h->bytes = mem_bytes;
@@ -237,7 +253,8 @@ ht_status table_set_words(ht_t* h, int words) {
 
 ht_status table_clear(ht_t* h, cudaStream_t s) {
   VSS_CUDA_TRY(cudaMemsetAsync(h->view.ctr, 0, sizeof(DevCounters), s));
-  VSS_CUDA_TRY(cudaMemsetAsync(h->view.buckets, 0, (size_t)(h->view.nb_mask + 1ull) * 4, s));
+  VSS_CUDA_TRY(cudaMemsetAsync(h->view.buckets, 0,
+                               (size_t)(h->view.nb_mask + 1ull) * (h->view.bucket_bits / 8), s));
   return HT_OK;
 }
 
@@ -325,7 +342,8 @@ ht_status ht_find_or_put(ht_t* h, const int32_t* keys_dev, uint64_t n, uint8_t* 
   const uint64_t want = (n + threads - 1) / threads;
   const uint64_t cap = (uint64_t)h->num_sms * 16;
   const int blocks = (int)(want < cap ? want : cap);
-  FopKernel k = pick_fop((int)h->view.nv, (int)h->params.line_buckets, h->params.dedup != 0);
+  FopKernel k = pick_fop((int)h->view.nv, (int)h->params.line_buckets, (int)h->view.bucket_bits,
+                         h->params.dedup != 0);
   k<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(h->view, keys_dev, n, seen_dev,
                                                                 idx_dev);
   VSS_CUDA_TRY(cudaGetLastError());

@@ -40,10 +40,8 @@ struct StreamSpec {
   uint64_t seed;
   uint64_t seed_key;      // mix(seed)
   uint64_t n_ids;
-  const uint32_t* zipf;   // ZIPF_CELLS + 1 entries, or null for uniform reuse
+  const uint32_t* zipf;   // 2^16 + 1 quantile entries, or null for uniform reuse
 };
-
-constexpr int kZipfCells = 1 << 16;
 
 __device__ __forceinline__ uint64_t call_id(const StreamSpec& s, uint64_t c) {
   const uint64_t i = c >> 1;
@@ -85,7 +83,7 @@ __global__ void __launch_bounds__(256) k_gen_keys(StreamSpec s, uint64_t c0, uin
 
 // Fused generator + find-or-put.  Counts new keys and sums the fingerprints
 // of the keys it stored (the set digest of the fill).
-template <int NV, int L, bool DEDUP>
+template <int NV, int L, bool DEDUP, int BW>
 __global__ void __launch_bounds__(256) k_find_or_put_stream(TableView t, StreamSpec s, uint64_t c0,
                                                             uint64_t n, unsigned long long* out) {
   LocalCounters lc;
@@ -120,7 +118,7 @@ __global__ void __launch_bounds__(256) k_find_or_put_stream(TableView t, StreamS
         if (valid && lead != (int)lane && diff == 0) probe = false;
       }
     }
-    if (probe) res = find_or_put<NV, L>(t, key, h, idx, lc);
+    if (probe) res = find_or_put<NV, L, false, BW>(t, key, h, idx, lc);
     if (res == FOP_NEW) {
       ++n_new;
       dig += fingerprint(key, t.state_words);
@@ -142,21 +140,27 @@ __global__ void __launch_bounds__(256) k_find_or_put_stream(TableView t, StreamS
 
 using StreamKernel = void (*)(TableView, StreamSpec, uint64_t, uint64_t, unsigned long long*);
 
+template <int NV, int L, int BW>
+static StreamKernel pick_stream_l(bool dedup) {
+  return dedup ? k_find_or_put_stream<NV, L, true, BW> : k_find_or_put_stream<NV, L, false, BW>;
+}
+
 template <int NV>
-static StreamKernel pick_stream_nv(int L, bool dedup) {
+static StreamKernel pick_stream_nv(int L, int bw, bool dedup) {
+  if (bw == 16) return L == 16 ? pick_stream_l<NV, 16, 16>(dedup) : pick_stream_l<NV, 32, 16>(dedup);
   switch (L) {
-    case 8: return dedup ? k_find_or_put_stream<NV, 8, true> : k_find_or_put_stream<NV, 8, false>;
-    case 16: return dedup ? k_find_or_put_stream<NV, 16, true> : k_find_or_put_stream<NV, 16, false>;
-    default: return dedup ? k_find_or_put_stream<NV, 32, true> : k_find_or_put_stream<NV, 32, false>;
+    case 8: return pick_stream_l<NV, 8, 32>(dedup);
+    case 16: return pick_stream_l<NV, 16, 32>(dedup);
+    default: return pick_stream_l<NV, 32, 32>(dedup);
   }
 }
 
-static StreamKernel pick_stream(int nv, int L, bool dedup) {
+static StreamKernel pick_stream(int nv, int L, int bw, bool dedup) {
   switch (nv) {
-    case 1: return pick_stream_nv<1>(L, dedup);
-    case 2: return pick_stream_nv<2>(L, dedup);
-    case 4: return pick_stream_nv<4>(L, dedup);
-    case 8: return pick_stream_nv<8>(L, dedup);
+    case 1: return pick_stream_nv<1>(L, bw, dedup);
+    case 2: return pick_stream_nv<2>(L, bw, dedup);
+    case 4: return pick_stream_nv<4>(L, bw, dedup);
+    case 8: return pick_stream_nv<8>(L, bw, dedup);
     default: return nullptr;
   }
 }
@@ -213,7 +217,8 @@ ht_status ht_find_or_put_stream(ht_t* h, uint64_t seed, uint64_t n_ids, uint64_t
                                 uint64_t n_calls, const uint32_t* zipf_table_dev,
                                 uint64_t* result_dev, void* stream) {
   if (!h || !result_dev || n_ids == 0 || call_begin + n_calls > 2 * n_ids) return HT_ERR_INVALID;
-  StreamKernel k = pick_stream((int)h->view.nv, (int)h->params.line_buckets, h->params.dedup != 0);
+  StreamKernel k = pick_stream((int)h->view.nv, (int)h->params.line_buckets,
+                               (int)h->view.bucket_bits, h->params.dedup != 0);
   if (!k) return HT_ERR_INVALID;
   if (n_calls == 0) return HT_OK;
   const StreamSpec s = make_spec(seed, n_ids, zipf_table_dev);

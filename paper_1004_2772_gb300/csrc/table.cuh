@@ -43,7 +43,7 @@ namespace vss {
 // One 32-byte bucket sector in one instruction.
 __device__ __forceinline__ void ld_sector(const uint32_t* p, uint4& a, uint4& b) {
 #if VSS_ACQ_MODE == 1
-  ld_acquire_v8(p, a, b);
+  ld_acquire_bucket_v8(p, a, b);
 #else
   ld_relaxed_v8(p, a, b);
 #endif
@@ -52,6 +52,82 @@ __device__ __forceinline__ void ld_sector(const uint32_t* p, uint4& a, uint4& b)
 struct LocalCounters {
   uint32_t busy_waits = 0;
   uint32_t rehashes = 0;
+};
+
+// Bucket word formats (Section 3.2: memoised hash plus the write bit), by width.
+// A 32-byte sector holds 8 buckets of 32 bits or 16 of 16 bits; `masks` turns
+// one sector, read as eight 32-bit words, into per-bucket bit masks: empty,
+// memo-equal (write or done) and done.
+template <int BW>
+struct Bucket;
+
+template <>
+struct Bucket<32> {
+  static constexpr int kPerSector = 8;
+  static constexpr uint32_t kDoneBit = kDone;
+  static constexpr uint32_t kMemoBits = kMemoMask;
+  __device__ static uint32_t memo(uint64_t h) { return memo_of(h); }
+  __device__ static void masks(const uint32_t (&wd)[8], uint32_t memo, uint32_t& emp, uint32_t& mem,
+                               uint32_t& dn) {
+    emp = 0;
+    mem = 0;
+    dn = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      emp |= (wd[k] == 0u ? 1u : 0u) << k;
+      mem |= ((wd[k] & kMemoMask) == memo ? 1u : 0u) << k;
+      dn |= (wd[k] >> 31) << k;
+    }
+  }
+  __device__ static uint32_t cas(uint32_t* buckets, uint32_t i, uint32_t val) {
+    return atomicCAS(buckets + i, 0u, val);
+  }
+  __device__ static void publish(uint32_t* buckets, uint32_t i, uint32_t val) {
+    st_relaxed(buckets + i, val);
+  }
+  __device__ static uint32_t load_acquire(const uint32_t* buckets, uint32_t i) {
+    return ld_acquire(buckets + i);
+  }
+  __device__ static uint32_t load_relaxed(const uint32_t* buckets, uint64_t i) {
+    return ld_relaxed(buckets + i);
+  }
+};
+
+template <>
+struct Bucket<16> {
+  static constexpr int kPerSector = 16;
+  static constexpr uint32_t kDoneBit = HT_BUCKET16_DONE;
+  static constexpr uint32_t kMemoBits = HT_BUCKET16_MEMO;
+  __device__ static uint32_t memo(uint64_t h) { return memo16_of(h); }
+  __device__ static void masks(const uint32_t (&wd)[8], uint32_t memo, uint32_t& emp, uint32_t& mem,
+                               uint32_t& dn) {
+    // bucket 2k is the low half of word k, bucket 2k+1 the high half
+    const uint32_t memo2 = memo * 0x10001u;
+    emp = 0;
+    mem = 0;
+    dn = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint32_t e = __vcmpeq2(wd[k], 0u);                      // 0xFFFF per empty half
+      const uint32_t m = __vcmpeq2(wd[k] & 0x7FFF7FFFu, memo2);    // per memo-equal half
+      emp |= ((e & 1u) | ((e >> 15) & 2u)) << (2 * k);
+      mem |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * k);
+      dn |= (((wd[k] >> 15) & 1u) | ((wd[k] >> 30) & 2u)) << (2 * k);
+    }
+  }
+  __device__ static uint32_t cas(uint32_t* buckets, uint32_t i, uint32_t val) {
+    return atomicCAS(reinterpret_cast<unsigned short*>(buckets) + i, (unsigned short)0,
+                     (unsigned short)val);
+  }
+  __device__ static void publish(uint32_t* buckets, uint32_t i, uint32_t val) {
+    st_relaxed_u16(reinterpret_cast<uint16_t*>(buckets) + i, val);
+  }
+  __device__ static uint32_t load_acquire(const uint32_t* buckets, uint32_t i) {
+    return ld_acquire_u16(reinterpret_cast<const uint16_t*>(buckets) + i);
+  }
+  __device__ static uint32_t load_relaxed(const uint32_t* buckets, uint64_t i) {
+    return ld_relaxed_u16(reinterpret_cast<const uint16_t*>(buckets) + i);
+  }
 };
 
 // Memory ordering of the publish step (Section 3.3: the data write must not be
@@ -74,32 +150,36 @@ __device__ __forceinline__ bool data_equal_after_done(const TableView& t, uint32
 
 // Wait while bucket i is in the write state (bounded, with nanosleep backoff).
 // Returns false on timeout (error latched).
+template <int BW>
 __device__ __forceinline__ bool wait_done(const TableView& t, uint32_t i, uint32_t& b,
                                           LocalCounters& lc) {
   uint32_t spins = 0, ns = 16;
   lc.busy_waits++;
-  while (!(b & kDone)) {
+  while (!(b & Bucket<BW>::kDoneBit)) {
     if (++spins > t.max_spin) {
       latch_error(t.ctr, HT_ERR_TIMEOUT);
       return false;
     }
     __nanosleep(ns);
     ns = ns < 256 ? ns * 2 : ns;
-    b = ld_acquire(t.buckets + i);
+    b = Bucket<BW>::load_acquire(t.buckets, i);
   }
   return true;
 }
 
-template <int NV, int L, bool RT = false>
+template <int NV, int L, bool RT = false, int BW = 32>
 __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& key, uint64_t h,
                                         uint32_t& out_idx, LocalCounters& lc) {
-  static_assert(L == 8 || L == 16 || L == 32, "line of 8, 16 or 32 buckets");
-  constexpr int NS = L / kSectorBuckets;  // sectors per line
-  const uint32_t memo = memo_of(h);
+  using Bk = Bucket<BW>;
+  constexpr int SB = Bk::kPerSector;      // buckets per 32-byte sector
+  constexpr uint32_t kAll = (1u << SB) - 1u;
+  static_assert(L % SB == 0 && L / SB >= 1 && L / SB <= 4, "line of 1, 2 or 4 sectors");
+  constexpr int NS = L / SB;              // sectors per line
+  const uint32_t memo = Bk::memo(h);
   const uint32_t index = (uint32_t)h & t.nb_mask;
   const uint32_t off = index & (L - 1);
-  const uint32_t s0 = off >> 3;          // first sector of the walk
-  const uint32_t p0 = off & 7;           // first position inside it
+  const uint32_t s0 = off / SB;           // first sector of the walk
+  const uint32_t p0 = off % SB;           // first position inside it
   const uint32_t step = (memo << 1) | 1u;
   uint32_t line = index / L;
 
@@ -110,29 +190,22 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
       line = (line + step) & t.lines_mask;
     }
     const uint32_t line_base = line * L;
-    // A sector is kept as three 8-bit masks (empty / memo-equal / done), not
-    // as its eight words: the walk only ever acts on empty or memo-equal
-    // buckets, whose words the masks determine.  f_* hold sector s0 for the
+    // A sector is kept as three bit masks (empty / memo-equal / done), not
+    // as its words: the walk only ever acts on empty or memo-equal buckets,
+    // whose words the masks determine.  f_* hold sector s0 for the
     // wrap-around part of the walk (a longer line visits it twice).
     uint32_t f_emp = 0, f_mem = 0, f_dn = 0;
 #pragma unroll 1
     for (int v = 0; v <= NS; ++v) {
       const uint32_t sec = (s0 + (uint32_t)v) & (NS - 1);
-      const uint32_t base = line_base + sec * 8;
+      const uint32_t base = line_base + sec * SB;
       uint32_t emp, mem, dn;
       if (v == 0 || v != NS) {
         uint4 a, b;
-        ld_sector(t.buckets + base, a, b);
+        // sector start in bytes: base * BW / 8, a multiple of 32
+        ld_sector(t.buckets + (size_t)base * BW / 32, a, b);
         const uint32_t wd[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-        emp = 0;
-        mem = 0;
-        dn = 0;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          emp |= (wd[k] == 0u ? 1u : 0u) << k;
-          mem |= ((wd[k] & kMemoMask) == memo ? 1u : 0u) << k;
-          dn |= (wd[k] >> 31) << k;
-        }
+        Bk::masks(wd, memo, emp, mem, dn);
         if (v == 0) {
           f_emp = emp;
           f_mem = mem;
@@ -144,7 +217,7 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
         dn = f_dn;
       }
       // positions of this visit, in walk order = ascending inside the sector
-      uint32_t todo = (v == 0) ? (0xFFu << p0) & 0xFFu : (v == NS) ? (1u << p0) - 1u : 0xFFu;
+      uint32_t todo = (v == 0) ? (kAll << p0) & kAll : (v == NS) ? (1u << p0) - 1u : kAll;
       while (todo) {
         const uint32_t cand = (emp | mem) & todo;
         if (!cand) break;
@@ -153,25 +226,25 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
         const uint32_t i = base + pos;
         bool acquired = (VSS_ACQ_MODE == 1);  // sector words came from acquire loads
         if (emp & bit) {
-          const uint32_t old = atomicCAS(t.buckets + i, 0u, memo);  // <memo, write>
+          const uint32_t old = Bk::cas(t.buckets, i, memo);  // <memo, write>
           if (old == 0u) {
             if (RT) store_row_rt<NV>(t.data + (size_t)i * t.nv, key, t.nv);
             else store_row<NV>(t.data + (size_t)i * NV, key);
             fence_acq_rel();                 // data before <memo, done>
-            st_relaxed(t.buckets + i, memo | kDone);
+            Bk::publish(t.buckets, i, memo | Bk::kDoneBit);
             out_idx = i;
             return FOP_NEW;
           }
           // another thread claimed it first: re-evaluate with the word it wrote
           acquired = false;  // a relaxed CAS result: fence before reading the row
           emp &= ~bit;
-          mem = ((old & kMemoMask) == memo) ? (mem | bit) : (mem & ~bit);
-          dn = (old & kDone) ? (dn | bit) : (dn & ~bit);
+          mem = ((old & Bk::kMemoBits) == memo) ? (mem | bit) : (mem & ~bit);
+          dn = (old & Bk::kDoneBit) ? (dn | bit) : (dn & ~bit);
         }
         if (mem & bit) {
-          uint32_t b = memo | ((dn & bit) ? kDone : 0u);
-          if (!(b & kDone)) {
-            if (!wait_done(t, i, b, lc)) return FOP_ERR;
+          uint32_t b = memo | ((dn & bit) ? Bk::kDoneBit : 0u);
+          if (!(b & Bk::kDoneBit)) {
+            if (!wait_done<BW>(t, i, b, lc)) return FOP_ERR;
             acquired = true;
           }
           if (data_equal_after_done<NV, RT>(t, i, key, acquired)) {

@@ -1,0 +1,48 @@
+"""The autotuner: its search space (host logic, no GPU) and, on the GPU, that
+every candidate of a tuning run reproduces the oracle's answer."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1004_2772_gb300 import autotune, synth
+
+
+def test_candidates_respect_line_lengths_per_width():
+    cands = list(autotune._candidates(autotune.TABLE_SPACE))
+    # 32-bit: 3 lines x 2 dedup x 2 block sizes; 16-bit: 2 lines x 2 x 2
+    assert len(cands) == 12 + 8
+    for c in cands:
+        assert c["line_buckets"] in autotune.LINES_FOR_WIDTH[c["bucket_bits"]]
+    assert len({tuple(sorted(c.items())) for c in cands}) == len(cands)
+    reach = list(autotune._candidates(autotune.REACH_SPACE))
+    assert len(reach) == (3 + 2) * 2
+
+
+def test_cache_round_trip(tmp_path):
+    path = str(tmp_path / "sub" / "cache.json")
+    autotune._save_cache(path, {"k": {"best": {"line_buckets": 8}}})
+    assert autotune._load_cache(path) == {"k": {"best": {"line_buckets": 8}}}
+    assert autotune._load_cache(str(tmp_path / "missing.json")) == {}
+
+
+@pytest.mark.gpu
+def test_tune_table_candidates_agree_with_oracle(cuda_lib, tmp_path):
+    n_log2, lf = 16, 0.5
+    n_ids = int(lf * (1 << n_log2))
+    space = {"line_buckets": (8, 16), "bucket_bits": (32, 16), "dedup": (0,), "block_threads": (256,)}
+    e = autotune.tune_table(n_log2, lf, "uniform", 16, seed=3, space=space, reps=1,
+                            cache_path=str(tmp_path / "c.json"))
+    ids = synth.call_ids(3, n_ids, 0, 2 * n_ids, "uniform")
+    ref = oracle.find_or_put_stream(synth.key_words(3, ids, 16))
+    assert e["n_new"] == ref.n_new == n_ids
+    assert int(e["digest"], 16) == ref.digest
+    assert len(e["all"]) == 3          # (32, 8), (32, 16), (16, 16)
+
+
+@pytest.mark.gpu
+def test_tune_reach_candidates_agree_with_oracle(cuda_lib, tmp_path):
+    m = synth.tiny_interleaving_model()
+    space = {"line_buckets": (8, 16), "bucket_bits": (32, 16), "block_threads": (256,)}
+    e = autotune.tune_reach(m, 18, space=space, reps=1, cache_path=str(tmp_path / "c.json"))
+    assert e["states"] == oracle.reach(m).states
+    assert len(e["all"]) == 3

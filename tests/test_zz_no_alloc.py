@@ -47,3 +47,13 @@ def test_no_alloc_refuses_oversized_requests(cuda_lib):
     assert st == b.HT_ERR_TOO_BIG
     st, r, levels = b.reach_noalloc(m, 18, max_levels=4096)  # still usable afterwards
     assert st == 0 and r.states == 100000
+
+
+def test_no_alloc_16_bit_buckets(cuda_lib):
+    b = cuda_lib
+    m = synth.tiny_interleaving_model()
+    ctx = b.ReachContext(18, m.state_words, max_levels=4096)
+    ref = ctx.reach(m)
+    ctx.close()
+    st, r, levels = b.reach_noalloc(m, 18, b.make_params(bucket_bits=16), max_levels=4096)
+    _same(st, r, levels, ref)
