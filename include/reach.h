@@ -106,6 +106,30 @@ ht_status ht_create_at(int log2_buckets, int state_words, const ht_params* param
                        uint64_t mem_bytes, ht_t** out);
 ht_status ht_destroy(ht_t* h);
 
+/* Tables of any size (Section 3.1: tables that fill the whole memory need sizes
+ * that are not powers of two; division by the invariant size makes that
+ * cheap).  n_buckets = lines * line_buckets, 16 <= n_buckets <= 2^31, any
+ * number of lines.  The line of a key is (h / line_buckets) mod lines, computed
+ * with one multiply-high by a constant prepared at creation (Granlund and
+ * Montgomery 1994, unsigned case); the offset inside the line is h mod
+ * line_buckets, as for power-of-two tables.  Rehash steps are 1 + a fraction
+ * of (lines - 1) taken from the memo: with a prime number of lines every line
+ * is reachable, with a composite one a key may see only the lines of one
+ * residue class before HT_ERR_FULL.  A power-of-two n_buckets behaves exactly
+ * like the log2 entry points.  Same ownership and errors as the log2 forms. */
+ht_status ht_bytes_n(uint64_t n_buckets, int state_words, uint64_t* bytes);
+ht_status ht_create_n_at(uint64_t n_buckets, int state_words, const ht_params* params, void* mem_dev,
+                         uint64_t mem_bytes, ht_t** out);
+/* The largest table whose block fits in `bytes` and whose line count is prime
+ * (or a power of two), for params' line length.  HT_ERR_OOM if none fits.
+ * Host only; no device call. */
+ht_status ht_buckets_for_bytes(uint64_t bytes, int state_words, const ht_params* params,
+                               uint64_t* n_buckets);
+/* The division above, on the host, for checking: q[i] = n[i] / d, r[i] = n[i]
+ * mod d for count 64-bit values, 1 <= d < 2^32.  Host only. */
+ht_status vss_line_divide(uint32_t d, const uint64_t* n_host, uint64_t count, uint64_t* q_host,
+                          uint32_t* r_host);
+
 /* Empty the table and zero its counters and error word (enqueued on stream). */
 ht_status ht_clear(ht_t* h, void* stream);
 
@@ -240,6 +264,16 @@ ht_status reach_ctx_create_at(int log2_buckets, int max_state_words, uint32_t ma
                               const ht_params* params, void* mem_dev, uint64_t mem_bytes,
                               reach_ctx_t** out);
 ht_status reach_ctx_destroy(reach_ctx_t* c);
+/* Contexts of any table size (see ht_bytes_n): the frontiers and trace arrays
+ * have n_buckets entries.  reach_ctx_buckets_for_bytes: the largest context
+ * with a prime line count whose block fits in `bytes` (host only). */
+ht_status reach_ctx_bytes_n(uint64_t n_buckets, int max_state_words, uint32_t max_levels,
+                            uint64_t* bytes);
+ht_status reach_ctx_create_n_at(uint64_t n_buckets, int max_state_words, uint32_t max_levels,
+                                const ht_params* params, void* mem_dev, uint64_t mem_bytes,
+                                reach_ctx_t** out);
+ht_status reach_ctx_buckets_for_bytes(uint64_t bytes, int max_state_words, uint32_t max_levels,
+                                      const ht_params* params, uint64_t* n_buckets);
 
 /* Validate the model and init (host) and upload both (enqueued on stream). */
 ht_status reach_ctx_load(reach_ctx_t* c, const reach_model* m, const int32_t* init_host,

@@ -37,6 +37,8 @@ EXPORTED = [
     "reach_batch_run", "reach_batch_results", "reach_batch_last_timing",
     "serve_bytes", "serve_open_at", "serve_open", "serve_submit", "serve_poll", "serve_status",
     "serve_close", "reach_ctx_deadlock_trace",
+    "ht_bytes_n", "ht_create_n_at", "ht_buckets_for_bytes", "vss_line_divide",
+    "reach_ctx_bytes_n", "reach_ctx_create_n_at", "reach_ctx_buckets_for_bytes",
 ]
 
 
@@ -148,6 +150,15 @@ def load(path: str | None = None) -> ctypes.CDLL:
                           ctypes.c_uint32, ctypes.POINTER(reach_result)],
         "reach": [_VP, ctypes.POINTER(reach_model), _VP, _i, _VP, _VP, ctypes.c_uint32,
                   ctypes.POINTER(reach_result)],
+        "ht_bytes_n": [_u64, _i, ctypes.POINTER(_u64)],
+        "ht_create_n_at": [_u64, _i, ctypes.POINTER(ht_params), _VP, _u64, ctypes.POINTER(_VP)],
+        "ht_buckets_for_bytes": [_u64, _i, ctypes.POINTER(ht_params), ctypes.POINTER(_u64)],
+        "vss_line_divide": [ctypes.c_uint32, _VP, _u64, _VP, _VP],
+        "reach_ctx_bytes_n": [_u64, _i, ctypes.c_uint32, ctypes.POINTER(_u64)],
+        "reach_ctx_create_n_at": [_u64, _i, ctypes.c_uint32, ctypes.POINTER(ht_params), _VP, _u64,
+                                  ctypes.POINTER(_VP)],
+        "reach_ctx_buckets_for_bytes": [_u64, _i, ctypes.c_uint32, ctypes.POINTER(ht_params),
+                                        ctypes.POINTER(_u64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -224,6 +235,60 @@ def ht_arrays(h: int) -> tuple[int, int, int]:
     b, d, rw = _VP(), _VP(), ctypes.c_uint32()
     _check(load().ht_arrays(h, ctypes.byref(b), ctypes.byref(d), ctypes.byref(rw)), "ht_arrays")
     return b.value, d.value, rw.value
+
+
+def ht_bytes_n(n_buckets: int, state_words: int) -> int:
+    out = _u64()
+    _check(load().ht_bytes_n(n_buckets, state_words, ctypes.byref(out)), "ht_bytes_n")
+    return out.value
+
+
+def ht_create_n_at(n_buckets, state_words, params, mem_dev: int, mem_bytes: int) -> int:
+    h = _VP()
+    _check(load().ht_create_n_at(n_buckets, state_words, ctypes.byref(params) if params else None,
+                                 mem_dev, mem_bytes, ctypes.byref(h)), "ht_create_n_at")
+    return h.value
+
+
+def ht_buckets_for_bytes(nbytes: int, state_words: int, params: ht_params | None = None) -> int:
+    out = _u64()
+    _check(load().ht_buckets_for_bytes(nbytes, state_words, ctypes.byref(params) if params else None,
+                                       ctypes.byref(out)), "ht_buckets_for_bytes")
+    return out.value
+
+
+def vss_line_divide(d: int, n) -> tuple[np.ndarray, np.ndarray]:
+    """(n // d, n % d) through the library's invariant-divisor division (host)."""
+    n = np.ascontiguousarray(n, dtype=np.uint64)
+    q = np.empty_like(n)
+    r = np.empty(n.shape, dtype=np.uint32)
+    _check(load().vss_line_divide(d, n.ctypes.data, n.size, q.ctypes.data, r.ctypes.data),
+           "vss_line_divide")
+    return q, r
+
+
+def reach_ctx_bytes_n(n_buckets: int, max_state_words: int, max_levels: int) -> int:
+    out = _u64()
+    _check(load().reach_ctx_bytes_n(n_buckets, max_state_words, max_levels, ctypes.byref(out)),
+           "reach_ctx_bytes_n")
+    return out.value
+
+
+def reach_ctx_create_n_at(n_buckets, max_state_words, max_levels, params, mem_dev, mem_bytes) -> int:
+    c = _VP()
+    _check(load().reach_ctx_create_n_at(n_buckets, max_state_words, max_levels,
+                                        ctypes.byref(params) if params else None, mem_dev, mem_bytes,
+                                        ctypes.byref(c)), "reach_ctx_create_n_at")
+    return c.value
+
+
+def reach_ctx_buckets_for_bytes(nbytes: int, max_state_words: int, max_levels: int,
+                                params: ht_params | None = None) -> int:
+    out = _u64()
+    _check(load().reach_ctx_buckets_for_bytes(nbytes, max_state_words, max_levels,
+                                              ctypes.byref(params) if params else None,
+                                              ctypes.byref(out)), "reach_ctx_buckets_for_bytes")
+    return out.value
 
 
 def reach_ctx_bytes(log2_buckets: int, max_state_words: int, max_levels: int) -> int:
@@ -382,15 +447,21 @@ def make_params(**kw) -> ht_params:
 class Table:
     """A find-or-put table whose device memory is a torch uint8 tensor."""
 
-    def __init__(self, log2_buckets: int, state_words: int, device="cuda", **params):
+    def __init__(self, log2_buckets: int | None, state_words: int, device="cuda",
+                 n_buckets: int | None = None, **params):
+        """2^log2_buckets buckets, or exactly n_buckets (log2_buckets None; any
+        multiple of the line length, see ht_create_n_at)."""
         torch = _torch()
+        if (log2_buckets is None) == (n_buckets is None):
+            raise ValueError("give exactly one of log2_buckets and n_buckets")
+        self.n_buckets = n_buckets if n_buckets is not None else 1 << log2_buckets
         self.log2_buckets, self.state_words = log2_buckets, state_words
         self.params = make_params(**params)
-        nbytes = ht_bytes(log2_buckets, state_words)
+        nbytes = ht_bytes_n(self.n_buckets, state_words)
         self.mem = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
         base = self.mem.data_ptr()
         aligned = (base + 255) // 256 * 256
-        self.handle = ht_create_at(log2_buckets, state_words, self.params, aligned, nbytes)
+        self.handle = ht_create_n_at(self.n_buckets, state_words, self.params, aligned, nbytes)
 
     def close(self):
         if self.handle:
@@ -474,7 +545,7 @@ class Table:
         int32 tensor [nb, row_words])."""
         torch = _torch()
         b, d, rw = ht_arrays(self.handle)
-        nb = 1 << self.log2_buckets
+        nb = self.n_buckets
         base = self.mem.data_ptr()
         if self.params.bucket_bits == 16:
             buckets = self.mem[b - base:b - base + 2 * nb].view(torch.int16)
@@ -499,16 +570,20 @@ class ReachOutput:
 class ReachContext:
     """Device-resident reachability context (table + frontiers), memory from torch."""
 
-    def __init__(self, log2_buckets: int, max_state_words: int, max_levels: int = 1 << 14,
-                 device="cuda", **params):
+    def __init__(self, log2_buckets: int | None, max_state_words: int, max_levels: int = 1 << 14,
+                 device="cuda", n_buckets: int | None = None, **params):
+        """2^log2_buckets buckets, or exactly n_buckets (log2_buckets None)."""
         torch = _torch()
+        if (log2_buckets is None) == (n_buckets is None):
+            raise ValueError("give exactly one of log2_buckets and n_buckets")
+        self.n_buckets = n_buckets if n_buckets is not None else 1 << log2_buckets
         self.log2_buckets, self.max_state_words, self.max_levels = log2_buckets, max_state_words, max_levels
         self.params = make_params(**params)
-        nbytes = reach_ctx_bytes(log2_buckets, max_state_words, max_levels)
+        nbytes = reach_ctx_bytes_n(self.n_buckets, max_state_words, max_levels)
         self.mem = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
         aligned = (self.mem.data_ptr() + 255) // 256 * 256
-        self.handle = reach_ctx_create_at(log2_buckets, max_state_words, max_levels, self.params,
-                                          aligned, nbytes)
+        self.handle = reach_ctx_create_n_at(self.n_buckets, max_state_words, max_levels, self.params,
+                                            aligned, nbytes)
 
     def close(self):
         if self.handle:

@@ -88,6 +88,8 @@ __device__ __forceinline__ TableView model_table(const BatchModel& M, const Batc
   t.state_words = M.W;
   t.nv = M.nv;
   t.bucket_bits = 32;
+  t.lines = lines;
+  t.lines_div = DivU64{0, 0, 0};  // power-of-two tables only
   return t;
 }
 
@@ -563,7 +565,7 @@ ht_status reach_batch_create_at(const reach_model* models, const int32_t* const*
   const uint64_t need = batch_layout_bytes(n_models, blob_words_total(blobs), max_levels, pool_bytes);
   if (mem_bytes < need) return HT_ERR_OOM;
   ht_params p{};
-  st = resolve_params(params, 10, &p);
+  st = resolve_params(params, 1u << 10, &p);
   if (st != HT_OK) return st;
   if (p.bucket_bits != 32) return HT_ERR_INVALID;  // batch tables use 32-bit buckets
   reach_batch_t* b = new (std::nothrow) reach_batch_t();

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "divide.h"
 #include "reach.h"
 
 namespace vss {
@@ -31,13 +32,15 @@ struct TableView {
   uint4* data;            // [nb * nv] rows of nv 16-byte chunks
   DevCounters* ctr;
   uint64_t seed;
-  uint32_t nb_mask;       // nb - 1
-  uint32_t lines_mask;    // nb / line_buckets - 1
+  uint32_t nb_mask;       // nb - 1 (power-of-two tables)
+  uint32_t lines_mask;    // lines - 1 (power-of-two tables)
   uint32_t max_rehash;
   uint32_t max_spin;
   uint32_t state_words;   // W
   uint32_t nv;            // ceil(W / 4)
   uint32_t bucket_bits;   // 32 or 16: width of a bucket word
+  uint32_t lines;         // nb / line_buckets
+  DivU64 lines_div;       // division by `lines`; m == 0 marks a power-of-two table
 };
 
 // ---------------------------------------------------------------------------

@@ -10,7 +10,7 @@
 struct ht {
   vss::TableView view{};
   ht_params params{};
-  int log2_nb = 0;
+  uint64_t nb = 0;  // buckets: 2^log2 or lines * line_buckets
   int max_words = 0;
   int num_sms = 0;
   uint64_t bytes = 0;
@@ -19,10 +19,16 @@ struct ht {
 };
 
 namespace vss {
-uint64_t table_bytes(int log2_nb, int max_words);
-ht_status resolve_params(const ht_params* in, int log2_nb, ht_params* out);
-ht_status table_init_at(ht_t* h, int log2_nb, int max_words, const ht_params* params, void* mem,
+// Table sizes are bucket counts nb: a power of two, or any multiple of the
+// line length whose line count fits 31 bits (constant division, Section 3.1).
+constexpr uint64_t kMaxBuckets = 1ull << 31;
+uint64_t table_bytes(uint64_t nb, int max_words);
+ht_status resolve_params(const ht_params* in, uint64_t nb, ht_params* out);
+ht_status table_init_at(ht_t* h, uint64_t nb, int max_words, const ht_params* params, void* mem,
                         uint64_t mem_bytes);
+// Largest nb <= max_nb that is line_buckets times a prime (or times a power
+// of two when max_nb is one); 0 if none.
+uint64_t prime_line_buckets(uint64_t max_nb, uint32_t line_buckets);
 ht_status table_set_words(ht_t* h, int words);
 ht_status table_clear(ht_t* h, cudaStream_t s);
 // Validate a model and pack it (with init) into the device blob format;

@@ -43,7 +43,7 @@ using namespace vss;
 
 struct reach_ctx {
   ht_t table;
-  int log2_nb = 0;
+  uint64_t nb = 0;
   int max_words = 0;
   uint32_t max_levels = 0;
   void* owned = nullptr;
@@ -69,14 +69,14 @@ struct reach_ctx {
   uint32_t last_launches = 0;
 };
 
-static uint64_t frontier_bytes(int log2_nb, int max_words) {
-  return align_up((1ull << log2_nb) * 16ull * (uint64_t)((max_words + 3) / 4), 256);
+static uint64_t frontier_bytes(uint64_t nb, int max_words) {
+  return align_up(nb * 16ull * (uint64_t)((max_words + 3) / 4), 256);
 }
 
-static uint64_t ctx_bytes(int log2_nb, int max_words, uint32_t max_levels) {
-  return align_up(table_bytes(log2_nb, max_words), 256) + align_up(kModelMaxWords * 4ull, 256) +
-         2 * frontier_bytes(log2_nb, max_words) + align_up(sizeof(ReachTotals), 256) +
-         2 * align_up((uint64_t)max_levels * 8, 256) + 3 * align_up((1ull << log2_nb) * 4, 256);
+static uint64_t ctx_bytes(uint64_t nb, int max_words, uint32_t max_levels) {
+  return align_up(table_bytes(nb, max_words), 256) + align_up(kModelMaxWords * 4ull, 256) +
+         2 * frontier_bytes(nb, max_words) + align_up(sizeof(ReachTotals), 256) +
+         2 * align_up((uint64_t)max_levels * 8, 256) + 3 * align_up(nb * 4, 256);
 }
 
 namespace vss {
@@ -165,7 +165,7 @@ static ReachDev make_rd(reach_ctx_t* c) {
   rd.smem_words = c->smem_words;
   rd.frontier0 = c->frontier0;
   rd.frontier1 = c->frontier1;
-  rd.cap = (uint32_t)(1ull << c->log2_nb);
+  rd.cap = (uint32_t)c->nb;
   rd.tot = c->tot;
   rd.level_sizes = c->level_sizes;
   rd.level_ns = c->level_ns;
@@ -184,29 +184,55 @@ static size_t smem_bytes_for(reach_ctx_t* c, int threads) {
 
 extern "C" {
 
-ht_status reach_ctx_bytes(int log2_buckets, int max_state_words, uint32_t max_levels,
-                          uint64_t* bytes) {
-  if (!bytes || log2_buckets < 4 || log2_buckets > 31 || max_state_words < 1 ||
+ht_status reach_ctx_bytes_n(uint64_t n_buckets, int max_state_words, uint32_t max_levels,
+                            uint64_t* bytes) {
+  if (!bytes || n_buckets < 16 || n_buckets > kMaxBuckets || max_state_words < 1 ||
       max_state_words > 32 || max_levels < 1)
     return HT_ERR_INVALID;
-  *bytes = ctx_bytes(log2_buckets, max_state_words, max_levels);
+  *bytes = ctx_bytes(n_buckets, max_state_words, max_levels);
   return HT_OK;
 }
 
-ht_status reach_ctx_create_at(int log2_buckets, int max_state_words, uint32_t max_levels,
-                              const ht_params* params, void* mem_dev, uint64_t mem_bytes,
-                              reach_ctx_t** out) {
+ht_status reach_ctx_bytes(int log2_buckets, int max_state_words, uint32_t max_levels,
+                          uint64_t* bytes) {
+  if (log2_buckets < 4 || log2_buckets > 31) return HT_ERR_INVALID;
+  return reach_ctx_bytes_n(1ull << log2_buckets, max_state_words, max_levels, bytes);
+}
+
+ht_status reach_ctx_buckets_for_bytes(uint64_t bytes, int max_state_words, uint32_t max_levels,
+                                      const ht_params* params, uint64_t* n_buckets) {
+  if (!n_buckets || max_state_words < 1 || max_state_words > 32 || max_levels < 1)
+    return HT_ERR_INVALID;
+  *n_buckets = 0;
+  ht_params p{};
+  ht_status st = resolve_params(params, 1u << 10, &p);
+  if (st != HT_OK) return st;
+  uint64_t lo = 0, hi = kMaxBuckets;  // ctx_bytes is increasing in nb
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo + 1) / 2;
+    if (ctx_bytes(mid, max_state_words, max_levels) <= bytes) lo = mid;
+    else hi = mid - 1;
+  }
+  const uint64_t nb = prime_line_buckets(lo, p.line_buckets);
+  if (nb == 0) return HT_ERR_OOM;
+  *n_buckets = nb;
+  return HT_OK;
+}
+
+ht_status reach_ctx_create_n_at(uint64_t n_buckets, int max_state_words, uint32_t max_levels,
+                                const ht_params* params, void* mem_dev, uint64_t mem_bytes,
+                                reach_ctx_t** out) {
   if (!out) return HT_ERR_INVALID;
   *out = nullptr;
   uint64_t need = 0;
-  ht_status st = reach_ctx_bytes(log2_buckets, max_state_words, max_levels, &need);
+  ht_status st = reach_ctx_bytes_n(n_buckets, max_state_words, max_levels, &need);
   if (st != HT_OK) return st;
   if (!mem_dev || (reinterpret_cast<uintptr_t>(mem_dev) & 255u)) return HT_ERR_INVALID;
   if (mem_bytes < need) return HT_ERR_OOM;
   reach_ctx_t* c = new (std::nothrow) reach_ctx_t();
   if (!c) return HT_ERR_OOM;
-  const uint64_t tb = align_up(table_bytes(log2_buckets, max_state_words), 256);
-  st = table_init_at(&c->table, log2_buckets, max_state_words, params, mem_dev, tb);
+  const uint64_t tb = align_up(table_bytes(n_buckets, max_state_words), 256);
+  st = table_init_at(&c->table, n_buckets, max_state_words, params, mem_dev, tb);
   if (st != HT_OK) {
     delete c;
     return st;
@@ -214,7 +240,7 @@ ht_status reach_ctx_create_at(int log2_buckets, int max_state_words, uint32_t ma
   char* p = static_cast<char*>(mem_dev) + tb;
   c->blob = reinterpret_cast<int*>(p);
   p += align_up(kModelMaxWords * 4ull, 256);
-  const uint64_t fb = frontier_bytes(log2_buckets, max_state_words);
+  const uint64_t fb = frontier_bytes(n_buckets, max_state_words);
   c->frontier0 = reinterpret_cast<uint4*>(p);
   p += fb;
   c->frontier1 = reinterpret_cast<uint4*>(p);
@@ -225,13 +251,13 @@ ht_status reach_ctx_create_at(int log2_buckets, int max_state_words, uint32_t ma
   p += align_up((uint64_t)max_levels * 8, 256);
   c->level_ns = reinterpret_cast<unsigned long long*>(p);
   p += align_up((uint64_t)max_levels * 8, 256);
-  const uint64_t ib = align_up((1ull << log2_buckets) * 4, 256);
+  const uint64_t ib = align_up(n_buckets * 4, 256);
   c->idx0 = reinterpret_cast<uint32_t*>(p);
   p += ib;
   c->idx1 = reinterpret_cast<uint32_t*>(p);
   p += ib;
   c->parent = reinterpret_cast<uint32_t*>(p);
-  c->log2_nb = log2_buckets;
+  c->nb = n_buckets;
   c->max_words = max_state_words;
   c->max_levels = max_levels;
   int dev = 0;
@@ -245,6 +271,17 @@ ht_status reach_ctx_create_at(int log2_buckets, int max_state_words, uint32_t ma
   }
   *out = c;
   return HT_OK;
+}
+
+ht_status reach_ctx_create_at(int log2_buckets, int max_state_words, uint32_t max_levels,
+                              const ht_params* params, void* mem_dev, uint64_t mem_bytes,
+                              reach_ctx_t** out) {
+  if (log2_buckets < 4 || log2_buckets > 31) {
+    if (out) *out = nullptr;
+    return HT_ERR_INVALID;
+  }
+  return reach_ctx_create_n_at(1ull << log2_buckets, max_state_words, max_levels, params, mem_dev,
+                               mem_bytes, out);
 }
 
 ht_status reach_ctx_create(int log2_buckets, int max_state_words, uint32_t max_levels,
@@ -539,13 +576,14 @@ extern "C" ht_status reach_noalloc(const reach_model* m, const int32_t* init_hos
 
   // carve the scratch array exactly like a context block
   ht_t table;
-  const uint64_t tb = align_up(table_bytes(log2_buckets, W), 256);
-  st = table_init_at(&table, log2_buckets, W, params, base, tb);
+  const uint64_t nb = 1ull << log2_buckets;
+  const uint64_t tb = align_up(table_bytes(nb, W), 256);
+  st = table_init_at(&table, nb, W, params, base, tb);
   if (st != HT_OK) return st;
   char* p = static_cast<char*>(base) + tb;
   int* blob = reinterpret_cast<int*>(p);
   p += align_up(kModelMaxWords * 4ull, 256);
-  const uint64_t fb = frontier_bytes(log2_buckets, W);
+  const uint64_t fb = frontier_bytes(nb, W);
   uint4* f0 = reinterpret_cast<uint4*>(p);
   p += fb;
   uint4* f1 = reinterpret_cast<uint4*>(p);
@@ -591,7 +629,7 @@ extern "C" ht_status reach_noalloc(const reach_model* m, const int32_t* init_hos
   rd.smem_words = smem_words;
   rd.frontier0 = f0;
   rd.frontier1 = f1;
-  rd.cap = (uint32_t)(1ull << log2_buckets);
+  rd.cap = (uint32_t)nb;
   rd.tot = tot;
   rd.level_sizes = lsz;
   rd.level_ns = lns;

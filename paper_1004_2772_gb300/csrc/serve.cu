@@ -226,7 +226,7 @@ ht_status serve_open_at(void* mem_dev, uint64_t mem_bytes, uint32_t n_slots, uin
   const uint64_t fixed = serve_fixed_bytes(n_slots, max_levels);
   if (mem_bytes < fixed + (1u << 20)) return HT_ERR_OOM;
   ht_params p{};
-  ht_status st = resolve_params(params, 10, &p);
+  ht_status st = resolve_params(params, 1u << 10, &p);
   if (st != HT_OK) return st;
   if (p.bucket_bits != 32) return HT_ERR_INVALID;  // batch tables use 32-bit buckets
   serve_t* s = new (std::nothrow) serve_t();

@@ -179,14 +179,13 @@ static ScanKernel pick_scan(int nv) {
 // ---------------------------------------------------------------------------
 static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
-uint64_t table_bytes(int log2_nb, int max_words) {
-  const uint64_t nb = 1ull << log2_nb;
+uint64_t table_bytes(uint64_t nb, int max_words) {
   const uint64_t nv = (uint64_t)((max_words + 3) / 4);
   return align_up(sizeof(DevCounters), 256) + align_up(nb * 4, 256) + align_up(nb * 16 * nv, 256) +
          256;  // scan scratch
 }
 
-ht_status resolve_params(const ht_params* in, int log2_nb, ht_params* out) {
+ht_status resolve_params(const ht_params* in, uint64_t nb, ht_params* out) {
   ht_params p{};
   if (in) p = *in;
   if (p.bucket_bits == 0) p.bucket_bits = 32;
@@ -199,8 +198,8 @@ ht_status resolve_params(const ht_params* in, int log2_nb, ht_params* out) {
   } else {
     return HT_ERR_INVALID;
   }
-  if ((1ull << log2_nb) < p.line_buckets) return HT_ERR_INVALID;
-  const uint64_t lines = (1ull << log2_nb) / p.line_buckets;
+  if (nb < p.line_buckets || nb % p.line_buckets) return HT_ERR_INVALID;
+  const uint64_t lines = nb / p.line_buckets;
   if (p.max_rehash == 0) p.max_rehash = (uint32_t)(lines < 4096 ? lines : 4096);
   if (p.max_spin == 0) p.max_spin = 1u << 18;
   if (p.block_threads == 0) p.block_threads = 256;
@@ -210,14 +209,15 @@ ht_status resolve_params(const ht_params* in, int log2_nb, ht_params* out) {
   return HT_OK;
 }
 
-ht_status table_init_at(ht_t* h, int log2_nb, int max_words, const ht_params* params, void* mem,
+static bool valid_nb(uint64_t nb) { return nb >= 16 && nb <= kMaxBuckets; }
+
+ht_status table_init_at(ht_t* h, uint64_t nb, int max_words, const ht_params* params, void* mem,
                         uint64_t mem_bytes) {
-  if (log2_nb < 4 || log2_nb > 31 || max_words < 1 || max_words > 32 || !mem) return HT_ERR_INVALID;
+  if (!valid_nb(nb) || max_words < 1 || max_words > 32 || !mem) return HT_ERR_INVALID;
   if ((reinterpret_cast<uintptr_t>(mem) & 255u) != 0) return HT_ERR_INVALID;
-  if (mem_bytes < table_bytes(log2_nb, max_words)) return HT_ERR_OOM;
-  ht_status st = resolve_params(params, log2_nb, &h->params);
+  ht_status st = resolve_params(params, nb, &h->params);
   if (st != HT_OK) return st;
-  const uint64_t nb = 1ull << log2_nb;
+  if (mem_bytes < table_bytes(nb, max_words)) return HT_ERR_OOM;
   const int nv = (max_words + 3) / 4;
   char* p = static_cast<char*>(mem);
   h->view.ctr = reinterpret_cast<DevCounters*>(p);
@@ -227,21 +227,41 @@ ht_status table_init_at(ht_t* h, int log2_nb, int max_words, const ht_params* pa
   h->view.data = reinterpret_cast<uint4*>(p);
   p += align_up(nb * 16 * (uint64_t)nv, 256);
   h->scan_scratch = reinterpret_cast<unsigned long long*>(p);
+  const uint64_t lines = nb / h->params.line_buckets;
+  const bool pow2 = (nb & (nb - 1)) == 0;
   h->view.seed = h->params.hash_seed;
-  h->view.nb_mask = (uint32_t)(nb - 1);
-  h->view.lines_mask = (uint32_t)(nb / h->params.line_buckets - 1);
+  h->view.nb_mask = pow2 ? (uint32_t)(nb - 1) : 0u;
+  h->view.lines_mask = pow2 ? (uint32_t)(lines - 1) : 0u;
+  h->view.lines = (uint32_t)lines;
+  h->view.lines_div = pow2 ? DivU64{0, 0, 0} : make_div((uint32_t)lines);
   h->view.max_rehash = h->params.max_rehash;
   h->view.max_spin = h->params.max_spin;
   h->view.state_words = (uint32_t)max_words;
   h->view.nv = (uint32_t)nv;
   h->view.bucket_bits = h->params.bucket_bits;
-  h->log2_nb = log2_nb;
+  h->nb = nb;
   h->max_words = max_words;
   h->bytes = mem_bytes;
   int dev = 0;
   VSS_CUDA_TRY(cudaGetDevice(&dev));
   VSS_CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
   return HT_OK;
+}
+
+static bool is_prime(uint64_t n) {
+  if (n < 2) return false;
+  if (n % 2 == 0) return n == 2;
+  for (uint64_t f = 3; f * f <= n; f += 2)
+    if (n % f == 0) return false;
+  return true;
+}
+
+uint64_t prime_line_buckets(uint64_t max_nb, uint32_t line_buckets) {
+  if (max_nb > kMaxBuckets) max_nb = kMaxBuckets;
+  if ((max_nb & (max_nb - 1)) == 0 && max_nb >= 16 && max_nb >= line_buckets) return max_nb;
+  for (uint64_t lines = max_nb / line_buckets; lines >= 2; --lines)
+    if (is_prime(lines) && lines * line_buckets >= 16) return lines * line_buckets;
+  return 0;
 }
 
 ht_status table_set_words(ht_t* h, int words) {
@@ -253,8 +273,7 @@ ht_status table_set_words(ht_t* h, int words) {
 
 ht_status table_clear(ht_t* h, cudaStream_t s) {
   VSS_CUDA_TRY(cudaMemsetAsync(h->view.ctr, 0, sizeof(DevCounters), s));
-  VSS_CUDA_TRY(cudaMemsetAsync(h->view.buckets, 0,
-                               (size_t)(h->view.nb_mask + 1ull) * (h->view.bucket_bits / 8), s));
+  VSS_CUDA_TRY(cudaMemsetAsync(h->view.buckets, 0, (size_t)h->nb * (h->view.bucket_bits / 8), s));
   return HT_OK;
 }
 
@@ -278,20 +297,24 @@ const char* ht_status_string(ht_status s) {
   }
 }
 
-ht_status ht_bytes(int log2_buckets, int state_words, uint64_t* bytes) {
-  if (!bytes || log2_buckets < 4 || log2_buckets > 31 || state_words < 1 || state_words > 32)
-    return HT_ERR_INVALID;
-  *bytes = table_bytes(log2_buckets, state_words);
+ht_status ht_bytes_n(uint64_t n_buckets, int state_words, uint64_t* bytes) {
+  if (!bytes || !valid_nb(n_buckets) || state_words < 1 || state_words > 32) return HT_ERR_INVALID;
+  *bytes = table_bytes(n_buckets, state_words);
   return HT_OK;
 }
 
-ht_status ht_create_at(int log2_buckets, int state_words, const ht_params* params, void* mem_dev,
-                       uint64_t mem_bytes, ht_t** out) {
+ht_status ht_bytes(int log2_buckets, int state_words, uint64_t* bytes) {
+  if (log2_buckets < 4 || log2_buckets > 31) return HT_ERR_INVALID;
+  return ht_bytes_n(1ull << log2_buckets, state_words, bytes);
+}
+
+ht_status ht_create_n_at(uint64_t n_buckets, int state_words, const ht_params* params, void* mem_dev,
+                         uint64_t mem_bytes, ht_t** out) {
   if (!out) return HT_ERR_INVALID;
   *out = nullptr;
   ht_t* h = new (std::nothrow) ht_t();
   if (!h) return HT_ERR_OOM;
-  ht_status st = table_init_at(h, log2_buckets, state_words, params, mem_dev, mem_bytes);
+  ht_status st = table_init_at(h, n_buckets, state_words, params, mem_dev, mem_bytes);
   if (st == HT_OK) st = table_clear(h, 0);
   if (st == HT_OK && cudaStreamSynchronize(0) != cudaSuccess) st = HT_ERR_CUDA;
   if (st != HT_OK) {
@@ -300,6 +323,15 @@ ht_status ht_create_at(int log2_buckets, int state_words, const ht_params* param
   }
   *out = h;
   return HT_OK;
+}
+
+ht_status ht_create_at(int log2_buckets, int state_words, const ht_params* params, void* mem_dev,
+                       uint64_t mem_bytes, ht_t** out) {
+  if (log2_buckets < 4 || log2_buckets > 31) {
+    if (out) *out = nullptr;
+    return HT_ERR_INVALID;
+  }
+  return ht_create_n_at(1ull << log2_buckets, state_words, params, mem_dev, mem_bytes, out);
 }
 
 ht_status ht_create(int log2_buckets, int state_words, const ht_params* params, ht_t** out) {
@@ -319,6 +351,37 @@ ht_status ht_create(int log2_buckets, int state_words, const ht_params* params, 
     return st;
   }
   (*out)->owned = mem;
+  return HT_OK;
+}
+
+ht_status ht_buckets_for_bytes(uint64_t bytes, int state_words, const ht_params* params,
+                               uint64_t* n_buckets) {
+  if (!n_buckets || state_words < 1 || state_words > 32) return HT_ERR_INVALID;
+  *n_buckets = 0;
+  ht_params p{};
+  ht_status st = resolve_params(params, 1u << 10, &p);
+  if (st != HT_OK) return st;
+  // table_bytes is increasing in nb: the largest nb that fits, then round down
+  uint64_t lo = 0, hi = kMaxBuckets;
+  while (lo < hi) {
+    const uint64_t mid = lo + (hi - lo + 1) / 2;
+    if (table_bytes(mid, state_words) <= bytes) lo = mid;
+    else hi = mid - 1;
+  }
+  const uint64_t nb = prime_line_buckets(lo, p.line_buckets);
+  if (nb == 0) return HT_ERR_OOM;
+  *n_buckets = nb;
+  return HT_OK;
+}
+
+ht_status vss_line_divide(uint32_t d, const uint64_t* n_host, uint64_t count, uint64_t* q_host,
+                          uint32_t* r_host) {
+  if (d == 0 || (count && (!n_host || !q_host || !r_host))) return HT_ERR_INVALID;
+  const DivU64 v = make_div(d);
+  for (uint64_t i = 0; i < count; ++i) {
+    q_host[i] = div_q(v, n_host[i]);
+    r_host[i] = div_r(v, n_host[i]);
+  }
   return HT_OK;
 }
 
@@ -366,7 +429,7 @@ ht_status ht_stats(ht_t* h, void* stream, ht_stats_t* out) {
   out->stored = c.stored;
   out->busy_waits = c.busy_waits;
   out->rehashes = c.rehashes;
-  out->capacity = 1ull << h->log2_nb;
+  out->capacity = h->nb;
   out->error = c.err;
   out->state_words = h->view.state_words;
   return HT_OK;
@@ -376,7 +439,7 @@ ht_status ht_scan(ht_t* h, void* stream, uint64_t* done, uint64_t* writing, uint
   if (!h) return HT_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   VSS_CUDA_TRY(cudaMemsetAsync(h->scan_scratch, 0, 3 * sizeof(unsigned long long), s));
-  const uint64_t nb = h->view.nb_mask + 1ull;
+  const uint64_t nb = h->nb;
   const uint64_t want = (nb + 255) / 256, cap = (uint64_t)h->num_sms * 8;
   pick_scan((int)h->view.nv)<<<(int)(want < cap ? want : cap), 256, 0, s>>>(h->view, nb,
                                                                             h->scan_scratch);

@@ -176,18 +176,35 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
   static_assert(L % SB == 0 && L / SB >= 1 && L / SB <= 4, "line of 1, 2 or 4 sectors");
   constexpr int NS = L / SB;              // sectors per line
   const uint32_t memo = Bk::memo(h);
-  const uint32_t index = (uint32_t)h & t.nb_mask;
-  const uint32_t off = index & (L - 1);
+  const uint32_t off = (uint32_t)h & (L - 1);
   const uint32_t s0 = off / SB;           // first sector of the walk
   const uint32_t p0 = off % SB;           // first position inside it
-  const uint32_t step = (memo << 1) | 1u;
-  uint32_t line = index / L;
+  // line = (h / L) mod lines: a mask for power-of-two tables, otherwise a
+  // division by the invariant line count (Section 3.1).  The rehash step is
+  // odd for power-of-two line counts and in [1, lines - 1] otherwise (coprime
+  // to a prime line count), so the line sequence visits every line.
+  const bool pow2 = t.lines_div.m == 0;
+  uint32_t line, step;
+  if (pow2) {
+    line = ((uint32_t)h & t.nb_mask) / L;
+    step = (memo << 1) | 1u;
+  } else {
+    constexpr int kLog2L = L == 8 ? 3 : L == 16 ? 4 : L == 32 ? 5 : 6;
+    line = div_r(t.lines_div, h >> kLog2L);
+    constexpr int kMemoBits = BW == 32 ? 31 : 15;
+    step = 1u + __umulhi(memo << (32 - kMemoBits), t.lines - 1u);
+  }
 
   for (uint32_t r = 0; r <= t.max_rehash; ++r) {
     if (r) {
       lc.rehashes++;
       if ((r & 31) == 0 && ld_relaxed(&t.ctr->err) != 0) return FOP_ERR;  // another key failed
-      line = (line + step) & t.lines_mask;
+      if (pow2) {
+        line = (line + step) & t.lines_mask;
+      } else {
+        line += step;
+        line = line >= t.lines ? line - t.lines : line;
+      }
     }
     const uint32_t line_base = line * L;
     // A sector is kept as three bit masks (empty / memo-equal / done), not
