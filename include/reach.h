@@ -81,6 +81,15 @@ typedef struct {
   uint32_t bucket_bits;   /* bucket word width: 32 (default) or 16 (the layouts above).
                              ht_scan, ht_arrays and reach_* follow it; the batch
                              and serving entry points accept only 32 */
+  uint32_t group_lanes;   /* lanes per key in ht_find_or_put and ht_find_or_put_stream:
+                             1 (default) = one thread walks the line a 32-byte sector
+                             at a time; 2, 4 or 8 = a sub-warp group loads the whole
+                             line of 4*group_lanes 32-bit buckets (32, 64 or 128
+                             bytes) at once, combines the lanes' bucket masks with
+                             shuffles and writes / compares the row in 16-byte chunks
+                             (line_buckets must be 0 or 4*group_lanes, dedup 0).  The
+                             reach_*, batch and serving entry points accept only 1 */
+  uint32_t reserved;      /* must be 0 */
   uint64_t hash_seed;     /* seed of the table hash; default a fixed constant */
 } ht_params;
 

@@ -8,6 +8,8 @@ the tunable ones are
                    64- or 128-byte line, read one 32-byte sector at a time)
     bucket_bits    bucket width: 32 (31-bit memo) or 16 (15-bit memo, half the
                    bucket array, lines of 16 or 32 buckets)
+    group_lanes    lanes per key: 1 (a thread walks the line sector by sector)
+                   or 2, 4, 8 (a sub-warp group loads a line of 4G buckets)
     dedup          merge equal keys inside a warp before probing (hot keys)
     block_threads  threads per block of the batch / expansion kernels
     log2_buckets   table size for a given number of keys (the load factor)
@@ -32,7 +34,7 @@ from . import binding as B
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1004_2772_gb300_autotune.json")
 
 TABLE_SPACE = {"line_buckets": (8, 16, 32), "bucket_bits": (32, 16), "dedup": (0, 1),
-               "block_threads": (128, 256)}
+               "group_lanes": (1, 2, 4, 8), "block_threads": (128, 256)}
 REACH_SPACE = {"line_buckets": (8, 16, 32), "bucket_bits": (32, 16), "block_threads": (128, 256)}
 
 # line lengths each bucket width supports (a line is 1, 2 or 4 sectors of 32 bytes)
@@ -61,6 +63,10 @@ def _candidates(space):
         cand = dict(zip(keys, vals))
         if cand.get("line_buckets", 0) not in LINES_FOR_WIDTH[cand.get("bucket_bits", 32)] + (0,):
             continue
+        g = cand.get("group_lanes", 1)
+        if g > 1 and (cand.get("line_buckets", 4 * g) != 4 * g or cand.get("bucket_bits", 32) != 32
+                      or cand.get("dedup", 0)):
+            continue  # a group reads one whole line of 4G 32-bit buckets
         yield cand
 
 

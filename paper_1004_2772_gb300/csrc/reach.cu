@@ -233,6 +233,7 @@ ht_status reach_ctx_create_n_at(uint64_t n_buckets, int max_state_words, uint32_
   if (!c) return HT_ERR_OOM;
   const uint64_t tb = align_up(table_bytes(n_buckets, max_state_words), 256);
   st = table_init_at(&c->table, n_buckets, max_state_words, params, mem_dev, tb);
+  if (st == HT_OK && c->table.params.group_lanes != 1) st = HT_ERR_INVALID;  // one thread per key
   if (st != HT_OK) {
     delete c;
     return st;
@@ -580,6 +581,7 @@ extern "C" ht_status reach_noalloc(const reach_model* m, const int32_t* init_hos
   const uint64_t tb = align_up(table_bytes(nb, W), 256);
   st = table_init_at(&table, nb, W, params, base, tb);
   if (st != HT_OK) return st;
+  if (table.params.group_lanes != 1) return HT_ERR_INVALID;
   char* p = static_cast<char*>(base) + tb;
   int* blob = reinterpret_cast<int*>(p);
   p += align_up(kModelMaxWords * 4ull, 256);

@@ -2,6 +2,7 @@
 #include <cstdlib>
 #include <new>
 
+#include "coop.cuh"
 #include "internal.h"
 #include "table.cuh"
 
@@ -88,6 +89,53 @@ __global__ void __launch_bounds__(256) k_find_or_put(TableView t, const int32_t*
   }
 }
 
+// Batched find-or-put with G lanes per key (coop.cuh): the group loads its
+// key (the same address in every lane), hashes it and probes whole lines.
+template <int NV, int G>
+__global__ void __launch_bounds__(256) k_find_or_put_group(TableView t, const int32_t* __restrict__ keys,
+                                                           uint64_t n, uint8_t* __restrict__ seen,
+                                                           uint32_t* __restrict__ idx) {
+  LocalCounters lc;
+  uint32_t stored = 0;
+  const uint32_t W = t.state_words;
+  const unsigned lane = lane_id();
+  const int gl = (int)(lane & (G - 1));
+  const unsigned gmask = ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+  const bool vec_ok = (W == 4u * NV) && ((reinterpret_cast<uintptr_t>(keys) & 15u) == 0);
+  const uint64_t groups = (uint64_t)gridDim.x * blockDim.x / G;
+  for (uint64_t k = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; k < n; k += groups) {
+    Vec<NV> key;
+    if (vec_ok) {
+      const uint4* src = reinterpret_cast<const uint4*>(keys + k * W);
+#pragma unroll
+      for (int j = 0; j < NV; ++j) key.c[j] = __ldg(src + j);
+    } else {
+      const int32_t* src = keys + k * W;
+      uint32_t w[4 * NV];
+#pragma unroll
+      for (int i = 0; i < 4 * NV; ++i) w[i] = i < (int)W ? (uint32_t)__ldg(src + i) : 0u;
+#pragma unroll
+      for (int j = 0; j < NV; ++j) key.c[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+    }
+    const uint64_t h = table_hash(key, W, t.seed);
+    uint32_t out = 0;
+    const int res = find_or_put_group<NV, G>(t, key, h, out, lc, gl, gmask);
+    if (gl == 0) {
+      seen[k] = (uint8_t)res;
+      if (idx) idx[k] = out;
+      stored += (res == FOP_NEW);
+    }
+  }
+  const uint32_t s = warp_sum(stored);
+  const uint32_t bw = warp_sum(lc.busy_waits);
+  const uint32_t rh = warp_sum(lc.rehashes);
+  if (lane == 0) {
+    if (s) atomicAdd(&t.ctr->stored, (unsigned long long)s);
+    if (bw) atomicAdd(&t.ctr->busy_waits, (unsigned long long)bw);
+    if (rh) atomicAdd(&t.ctr->rehashes, (unsigned long long)(rh / G));
+  }
+}
+
 // Full scan: done / write-state bucket counts and the digest of done rows.
 template <int NV>
 __global__ void __launch_bounds__(256) k_scan(TableView t, uint64_t nb, unsigned long long* out) {
@@ -147,7 +195,24 @@ static FopKernel pick_fop_nv(int L, int bw, bool dedup) {
   }
 }
 
-static FopKernel pick_fop(int nv, int L, int bw, bool dedup) {
+template <int G>
+static FopKernel pick_fop_group(int nv) {
+  switch (nv) {
+    case 1: return k_find_or_put_group<1, G>;
+    case 2: return k_find_or_put_group<2, G>;
+    case 3: return k_find_or_put_group<3, G>;
+    case 4: return k_find_or_put_group<4, G>;
+    case 5: return k_find_or_put_group<5, G>;
+    case 6: return k_find_or_put_group<6, G>;
+    case 7: return k_find_or_put_group<7, G>;
+    default: return k_find_or_put_group<8, G>;
+  }
+}
+
+static FopKernel pick_fop(int nv, int L, int bw, bool dedup, int group) {
+  if (group == 2) return pick_fop_group<2>(nv);
+  if (group == 4) return pick_fop_group<4>(nv);
+  if (group == 8) return pick_fop_group<8>(nv);
   switch (nv) {
     case 1: return pick_fop_nv<1>(L, bw, dedup);
     case 2: return pick_fop_nv<2>(L, bw, dedup);
@@ -189,6 +254,15 @@ ht_status resolve_params(const ht_params* in, uint64_t nb, ht_params* out) {
   ht_params p{};
   if (in) p = *in;
   if (p.bucket_bits == 0) p.bucket_bits = 32;
+  if (p.group_lanes == 0) p.group_lanes = 1;
+  if (p.reserved != 0) return HT_ERR_INVALID;
+  if (p.group_lanes != 1) {
+    // a group of G lanes reads a line of 4G 32-bit buckets at once
+    const uint32_t G = p.group_lanes;
+    if ((G != 2 && G != 4 && G != 8) || p.bucket_bits != 32 || p.dedup) return HT_ERR_INVALID;
+    if (p.line_buckets == 0) p.line_buckets = 4 * G;
+    if (p.line_buckets != 4 * G) return HT_ERR_INVALID;
+  }
   if (p.bucket_bits == 32) {
     if (p.line_buckets == 0) p.line_buckets = 8;
     if (p.line_buckets != 8 && p.line_buckets != 16 && p.line_buckets != 32) return HT_ERR_INVALID;
@@ -402,11 +476,11 @@ ht_status ht_find_or_put(ht_t* h, const int32_t* keys_dev, uint64_t n, uint8_t* 
   if (!h || (n && (!keys_dev || !seen_dev))) return HT_ERR_INVALID;
   if (n == 0) return HT_OK;
   const int threads = (int)h->params.block_threads;
-  const uint64_t want = (n + threads - 1) / threads;
+  const uint64_t want = (n * h->params.group_lanes + threads - 1) / threads;  // G lanes per key
   const uint64_t cap = (uint64_t)h->num_sms * 16;
   const int blocks = (int)(want < cap ? want : cap);
   FopKernel k = pick_fop((int)h->view.nv, (int)h->params.line_buckets, (int)h->view.bucket_bits,
-                         h->params.dedup != 0);
+                         h->params.dedup != 0, (int)h->params.group_lanes);
   k<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(h->view, keys_dev, n, seen_dev,
                                                                 idx_dev);
   VSS_CUDA_TRY(cudaGetLastError());

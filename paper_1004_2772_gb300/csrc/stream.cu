@@ -15,6 +15,7 @@
 // k_gen_keys materialises keys (for the batch API); k_find_or_put_stream
 // runs find-or-put on keys generated in registers, so the table is measured
 // without streaming keys from HBM.
+#include "coop.cuh"
 #include "internal.h"
 #include "table.cuh"
 
@@ -138,7 +139,54 @@ __global__ void __launch_bounds__(256) k_find_or_put_stream(TableView t, StreamS
   }
 }
 
+// The same with G lanes per key (coop.cuh); every lane of a group generates
+// the group's key.
+template <int NV, int G>
+__global__ void __launch_bounds__(256) k_find_or_put_stream_group(TableView t, StreamSpec s, uint64_t c0,
+                                                                  uint64_t n, unsigned long long* out) {
+  LocalCounters lc;
+  unsigned long long n_new = 0, dig = 0;
+  const unsigned lane = lane_id();
+  const int gl = (int)(lane & (G - 1));
+  const unsigned gmask = ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
+  const uint64_t groups = (uint64_t)gridDim.x * blockDim.x / G;
+  for (uint64_t k = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G; k < n; k += groups) {
+    Vec<NV> key;
+    key_of<NV>(s.seed, call_id(s, c0 + k), t.state_words, key);
+    const uint64_t h = table_hash(key, t.state_words, t.seed);
+    uint32_t idx = 0;
+    const int res = find_or_put_group<NV, G>(t, key, h, idx, lc, gl, gmask);
+    if (res == FOP_NEW && gl == 0) {
+      ++n_new;
+      dig += fingerprint(key, t.state_words);
+    }
+  }
+  n_new = warp_sum(n_new);
+  dig = warp_sum(dig);
+  const uint32_t bw = warp_sum(lc.busy_waits), rh = warp_sum(lc.rehashes);
+  if (lane == 0) {
+    if (n_new) {
+      atomicAdd(out + 0, n_new);
+      atomicAdd(&t.ctr->stored, n_new);
+    }
+    if (dig) atomicAdd(out + 1, dig);
+    if (bw) atomicAdd(&t.ctr->busy_waits, (unsigned long long)bw);
+    if (rh) atomicAdd(&t.ctr->rehashes, (unsigned long long)(rh / G));
+  }
+}
+
 using StreamKernel = void (*)(TableView, StreamSpec, uint64_t, uint64_t, unsigned long long*);
+
+template <int G>
+static StreamKernel pick_stream_group(int nv) {
+  switch (nv) {
+    case 1: return k_find_or_put_stream_group<1, G>;
+    case 2: return k_find_or_put_stream_group<2, G>;
+    case 4: return k_find_or_put_stream_group<4, G>;
+    case 8: return k_find_or_put_stream_group<8, G>;
+    default: return nullptr;
+  }
+}
 
 template <int NV, int L, int BW>
 static StreamKernel pick_stream_l(bool dedup) {
@@ -155,7 +203,10 @@ static StreamKernel pick_stream_nv(int L, int bw, bool dedup) {
   }
 }
 
-static StreamKernel pick_stream(int nv, int L, int bw, bool dedup) {
+static StreamKernel pick_stream(int nv, int L, int bw, bool dedup, int group) {
+  if (group == 2) return pick_stream_group<2>(nv);
+  if (group == 4) return pick_stream_group<4>(nv);
+  if (group == 8) return pick_stream_group<8>(nv);
   switch (nv) {
     case 1: return pick_stream_nv<1>(L, bw, dedup);
     case 2: return pick_stream_nv<2>(L, bw, dedup);
@@ -218,12 +269,14 @@ ht_status ht_find_or_put_stream(ht_t* h, uint64_t seed, uint64_t n_ids, uint64_t
                                 uint64_t* result_dev, void* stream) {
   if (!h || !result_dev || n_ids == 0 || call_begin + n_calls > 2 * n_ids) return HT_ERR_INVALID;
   StreamKernel k = pick_stream((int)h->view.nv, (int)h->params.line_buckets,
-                               (int)h->view.bucket_bits, h->params.dedup != 0);
+                               (int)h->view.bucket_bits, h->params.dedup != 0,
+                               (int)h->params.group_lanes);
   if (!k) return HT_ERR_INVALID;
   if (n_calls == 0) return HT_OK;
   const StreamSpec s = make_spec(seed, n_ids, zipf_table_dev);
   const int threads = (int)h->params.block_threads;
-  const uint64_t want = (n_calls + threads - 1) / threads, cap = (uint64_t)h->num_sms * 16;
+  const uint64_t lanes = n_calls * h->params.group_lanes;  // G lanes per key in group mode
+  const uint64_t want = (lanes + threads - 1) / threads, cap = (uint64_t)h->num_sms * 16;
   const int blocks = (int)(want < cap ? want : cap);
   k<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
       h->view, s, call_begin, n_calls, reinterpret_cast<unsigned long long*>(result_dev));

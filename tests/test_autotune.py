@@ -9,10 +9,14 @@ from paper_1004_2772_gb300 import autotune, synth
 
 def test_candidates_respect_line_lengths_per_width():
     cands = list(autotune._candidates(autotune.TABLE_SPACE))
-    # 32-bit: 3 lines x 2 dedup x 2 block sizes; 16-bit: 2 lines x 2 x 2
-    assert len(cands) == 12 + 8
+    # one lane per key: 32-bit 3 lines x 2 dedup x 2 block sizes, 16-bit 2 x 2 x 2;
+    # groups of 2, 4, 8 lanes: one line each (32-bit, no dedup) x 2 block sizes
+    assert len(cands) == 12 + 8 + 3 * 2
     for c in cands:
         assert c["line_buckets"] in autotune.LINES_FOR_WIDTH[c["bucket_bits"]]
+        if c["group_lanes"] > 1:
+            assert c["line_buckets"] == 4 * c["group_lanes"] and c["bucket_bits"] == 32
+            assert c["dedup"] == 0
     assert len({tuple(sorted(c.items())) for c in cands}) == len(cands)
     reach = list(autotune._candidates(autotune.REACH_SPACE))
     assert len(reach) == (3 + 2) * 2
