@@ -305,6 +305,12 @@ ht_status reach_ctx_result(reach_ctx_t* c, void* stream, uint64_t* level_sizes_h
  * the events. */
 ht_status reach_ctx_last_timing(reach_ctx_t* c, float* kernel_ms, uint32_t* launches);
 
+/* The same device time for each of the most recent runs (at most 64 are
+ * kept): ms_host[0..*got) = min(n, runs kept) durations, oldest first, so a
+ * caller can time every launch of a loop without synchronising inside it.
+ * Waits on the last run's end event. */
+ht_status reach_ctx_run_times(reach_ctx_t* c, uint32_t n, float* ms_host, uint32_t* got);
+
 /* Level start times of the last REACH_PERSISTENT run: level_ns_host[k] is the
  * device %globaltimer (ns) when level k began (k = 0: after init was
  * inserted).  Synchronises `stream`; *n_levels = entries written. */

@@ -39,6 +39,7 @@ EXPORTED = [
     "serve_close", "reach_ctx_deadlock_trace",
     "ht_bytes_n", "ht_create_n_at", "ht_buckets_for_bytes", "vss_line_divide",
     "reach_ctx_bytes_n", "reach_ctx_create_n_at", "reach_ctx_buckets_for_bytes",
+    "reach_ctx_run_times",
 ]
 
 
@@ -151,6 +152,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                           ctypes.c_uint32, ctypes.POINTER(reach_result)],
         "reach": [_VP, ctypes.POINTER(reach_model), _VP, _i, _VP, _VP, ctypes.c_uint32,
                   ctypes.POINTER(reach_result)],
+        "reach_ctx_run_times": [_VP, ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_uint32)],
         "ht_bytes_n": [_u64, _i, ctypes.POINTER(_u64)],
         "ht_create_n_at": [_u64, _i, ctypes.POINTER(ht_params), _VP, _u64, ctypes.POINTER(_VP)],
         "ht_buckets_for_bytes": [_u64, _i, ctypes.POINTER(ht_params), ctypes.POINTER(_u64)],
@@ -633,6 +635,14 @@ class ReachContext:
         if n.value == 0:
             return None, buf[:0]
         return int(lv.value), buf[:n.value]
+
+    def run_times(self, n: int) -> np.ndarray:
+        """Kernel device times (ms) of the last n runs (at most 64), oldest first."""
+        out = np.zeros(n, dtype=np.float32)
+        got = ctypes.c_uint32()
+        _check(load().reach_ctx_run_times(self.handle, n, out.ctypes.data, ctypes.byref(got)),
+               "reach_ctx_run_times")
+        return out[:got.value]
 
     def level_ns(self) -> np.ndarray:
         """Device timestamps (ns) of the level starts of the last persistent run."""

@@ -41,6 +41,8 @@ static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
 using namespace vss;
 
+constexpr int kTimingRing = 64;  // kernel timings kept per context
+
 struct reach_ctx {
   ht_t table;
   uint64_t nb = 0;
@@ -65,7 +67,9 @@ struct reach_ctx {
   std::vector<unsigned long long> host_levels;  // per-level mode
   ht_status host_status = HT_OK;
   int coop = 0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // start / end events of the expansion kernels of the last kTimingRing runs
+  cudaEvent_t ev[kTimingRing][2] = {};
+  uint64_t runs = 0;  // runs started; run r uses slot r % kTimingRing
   uint32_t last_launches = 0;
 };
 
@@ -264,11 +268,17 @@ ht_status reach_ctx_create_n_at(uint64_t n_buckets, int max_state_words, uint32_
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
-      cudaMallocHost(&c->host_tot, sizeof(ReachTotals)) != cudaSuccess ||
-      cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+      cudaMallocHost(&c->host_tot, sizeof(ReachTotals)) != cudaSuccess) {
     cudaGetLastError();
-    delete c;
+    reach_ctx_destroy(c);
     return HT_ERR_CUDA;
+  }
+  for (int i = 0; i < kTimingRing; ++i) {
+    if (cudaEventCreate(&c->ev[i][0]) != cudaSuccess || cudaEventCreate(&c->ev[i][1]) != cudaSuccess) {
+      cudaGetLastError();
+      reach_ctx_destroy(c);
+      return HT_ERR_CUDA;
+    }
   }
   *out = c;
   return HT_OK;
@@ -309,20 +319,35 @@ ht_status reach_ctx_create(int log2_buckets, int max_state_words, uint32_t max_l
 ht_status reach_ctx_destroy(reach_ctx_t* c) {
   if (!c) return HT_ERR_INVALID;
   if (c->host_tot) cudaFreeHost(c->host_tot);
-  if (c->ev0) cudaEventDestroy(c->ev0);
-  if (c->ev1) cudaEventDestroy(c->ev1);
+  for (int i = 0; i < kTimingRing; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (c->ev[i][j]) cudaEventDestroy(c->ev[i][j]);
   if (c->owned) cudaFree(c->owned);
   delete c;
   return HT_OK;
 }
 
 ht_status reach_ctx_last_timing(reach_ctx_t* c, float* kernel_ms, uint32_t* launches) {
-  if (!c || c->last_mode < 0) return HT_ERR_INVALID;
-  VSS_CUDA_TRY(cudaEventSynchronize(c->ev1));
+  if (!c || c->last_mode < 0 || c->runs == 0) return HT_ERR_INVALID;
+  const int slot = (int)((c->runs - 1) % kTimingRing);
+  VSS_CUDA_TRY(cudaEventSynchronize(c->ev[slot][1]));
   float ms = 0.f;
-  VSS_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+  VSS_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev[slot][0], c->ev[slot][1]));
   if (kernel_ms) *kernel_ms = ms;
   if (launches) *launches = c->last_launches;
+  return HT_OK;
+}
+
+ht_status reach_ctx_run_times(reach_ctx_t* c, uint32_t n, float* ms_host, uint32_t* got) {
+  if (!c || (n && !ms_host)) return HT_ERR_INVALID;
+  uint64_t avail = c->runs < (uint64_t)kTimingRing ? c->runs : (uint64_t)kTimingRing;
+  const uint32_t k = (uint32_t)(avail < n ? avail : n);
+  if (k) VSS_CUDA_TRY(cudaEventSynchronize(c->ev[(c->runs - 1) % kTimingRing][1]));
+  for (uint32_t i = 0; i < k; ++i) {
+    const int slot = (int)((c->runs - k + i) % kTimingRing);
+    VSS_CUDA_TRY(cudaEventElapsedTime(&ms_host[i], c->ev[slot][0], c->ev[slot][1]));
+  }
+  if (got) *got = k;
   return HT_OK;
 }
 
@@ -422,10 +447,12 @@ ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
     if (per_sm < 1) return HT_ERR_INVALID;
     const int blocks = per_sm * c->table.num_sms;
     void* args[] = {&tv, &rd};
-    VSS_CUDA_TRY(cudaEventRecord(c->ev0, s));
+    cudaEvent_t* ev = c->ev[c->runs % kTimingRing];
+    VSS_CUDA_TRY(cudaEventRecord(ev[0], s));
     VSS_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(kern), blocks, threads, args,
                                              smem, s));
-    VSS_CUDA_TRY(cudaEventRecord(c->ev1, s));
+    VSS_CUDA_TRY(cudaEventRecord(ev[1], s));
+    c->runs++;
     c->last_launches = 1;
     return HT_OK;
   }
@@ -434,7 +461,9 @@ ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
   int per_sm = 0;
   VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.level, threads, smem));
   if (per_sm < 1) return HT_ERR_INVALID;
-  VSS_CUDA_TRY(cudaEventRecord(c->ev0, s));
+  cudaEvent_t* ev = c->ev[c->runs % kTimingRing];
+  c->runs++;
+  VSS_CUDA_TRY(cudaEventRecord(ev[0], s));
   ks.seed<<<1, 1, 0, s>>>(tv, rd);
   VSS_CUDA_TRY(cudaGetLastError());
   c->last_launches = 1;
@@ -449,7 +478,7 @@ ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
     VSS_CUDA_TRY(cudaMemsetAsync(&c->tot->cursor[k % 3], 0, 4, s));
     ks.level<<<blocks, threads, smem, s>>>(tv, rd, k);
     VSS_CUDA_TRY(cudaGetLastError());
-    VSS_CUDA_TRY(cudaEventRecord(c->ev1, s));
+    VSS_CUDA_TRY(cudaEventRecord(ev[1], s));
     c->last_launches++;
     VSS_CUDA_TRY(cudaMemcpyAsync(c->host_tot, c->tot, sizeof(ReachTotals), cudaMemcpyDeviceToHost, s));
     uint32_t err = 0;

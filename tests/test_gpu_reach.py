@@ -208,3 +208,16 @@ def test_no_deadlock_no_trace(cuda_lib):
     ctx.reach(m, mode=cuda_lib.REACH_PERSISTENT | cuda_lib.REACH_TRACE)
     level, path = ctx.deadlock_trace()
     assert level is None and path.shape[0] == 0
+
+
+def test_run_times_ring(cuda_lib):
+    """Every launch of a loop keeps its own kernel time (no sync inside the loop)."""
+    m = synth.tiny_interleaving_model()
+    ctx = cuda_lib.ReachContext(18, 5, max_levels=256)
+    ctx.load(m)
+    for _ in range(70):                   # more runs than the ring keeps
+        ctx.run(cuda_lib.REACH_PERSISTENT)
+    t = ctx.run_times(100)
+    assert t.shape[0] == 64 and (t > 0).all()
+    assert abs(float(t[-1]) - ctx.last_timing()[0]) < 1e-6
+    assert ctx.result().states == 100000
