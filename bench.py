@@ -42,6 +42,7 @@ WORKLOADS = {
     "tiny": (None, 18),
     # not reachability of one model: see run_hashtable / run_batch / run_serve
     "hashtable": (None, 26),
+    "hashtable-sweep": (None, 0),
     "batch": (None, 0),
     "serve": (None, 0),
 }
@@ -50,7 +51,7 @@ MAX_LEVELS = 1 << 14
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_reach_persistent launch on
 # the full BEEM-shaped workload (ncu, 1 pass; profiles/k_reach_persistent_beem-shaped.md).
 # Must be re-measured (or set to None) whenever the kernel changes.
-NCU_TRAFFIC_BYTES = {"beem": 24.21e9}
+NCU_TRAFFIC_BYTES = {"beem": 24.12e9}
 
 
 def workload_model(name="beem"):
@@ -245,7 +246,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="persistent", choices=["persistent", "per-level"])
-    ap.add_argument("--line-buckets", type=int, default=8)
+    ap.add_argument("--line-buckets", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="beem", choices=sorted(WORKLOADS))
     ap.add_argument("--log2-buckets", type=int, default=0, help="0 = the workload's size")
@@ -269,9 +270,9 @@ def main():
     dev = torch.device("cuda", local)
     _build.build()
     binding.load()
-    if args.workload in ("hashtable", "batch", "serve"):
-        {"hashtable": run_hashtable, "batch": run_batch, "serve": run_serve}[args.workload](
-            args, world, rank, local, dev)
+    if args.workload in ("hashtable", "hashtable-sweep", "batch", "serve"):
+        {"hashtable": run_hashtable, "hashtable-sweep": run_hashtable_sweep, "batch": run_batch,
+         "serve": run_serve}[args.workload](args, world, rank, local, dev)
         return
 
     # random-access rates of this GPU (the random-sector roofline's denominators)
@@ -332,6 +333,13 @@ def main():
     d2h = 64 + 64 + 8 * len(r.level_sizes)
 
     peak, which = peaks()
+    tab_bytes = binding.ht_bytes(LOG2_BUCKETS, model.state_words)
+    if tab_bytes > 129e6:
+        l2_note = (f"inputs larger than L2 ({tab_bytes / 1e9:.1f} GB table per step; bucket array "
+                   f"{(4 << LOG2_BUCKETS) >> 20} MiB)")
+    else:
+        l2_note = (f"L2-resident working set ({tab_bytes / 1e6:.0f} MB table), not flushed between "
+                   "steps: a latency-bound configuration")
     alg = algorithmic_bytes(got.states, got.transitions, model.state_words)
     achieved = alg / (kernel_ms / 1000.0) / 1e9
     line = {
@@ -343,7 +351,7 @@ def main():
                    "levels": len(got.level_sizes), "state_words": model.state_words,
                    "log2_buckets": LOG2_BUCKETS, "line_buckets": args.line_buckets,
                    "mode": args.mode, "parallelism": f"replicas{world}" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (4.3 GB table per step; bucket array 256 MiB)"},
+                   "l2": l2_note},
         "find_or_put_ops_per_s": trans_all / (t_max / 1000.0),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
@@ -438,6 +446,82 @@ def run_hashtable(args, world, rank, local, dev):
     line["clocks"] = clocks.summary()
     if tuned:
         line["autotune"] = {"best": tuned["best"], "candidates": len(tuned["all"])}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def hashtable_bound_s(calls, n_ids, rates, api):
+    """Seconds the fill would take at the probe-measured random-access rates:
+    a 32 B sector read per call, a 64 B row read per repeat, a sector CAS plus
+    a 64 B row write per new key (streamed keys and outputs at copy speed)."""
+    dup, new = calls - n_ids, n_ids
+    t = calls / rates[0] + dup / rates[1] + 3 * new / rates[2]
+    if api:
+        t += calls * (64 + 5) / (peaks()[0] * 1e9)
+    return t
+
+
+def run_hashtable_sweep(args, world, rank, local, dev):
+    """The hash-table benchmark grid: 2^n buckets for n in 24..28, load factors
+    0.5 / 0.75 / 0.9, uniform and Zipf(1.1) reuse, keys in registers (fused)
+    and materialised (batch API); at least 10^9 timed calls per point (whole
+    fills repeated).  value = calls/s at 2^26, LF 0.75, uniform, fused."""
+    import torch
+    from paper_1004_2772_gb300 import binding, synth
+    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
+    min_calls = int(float(os.environ.get("BENCH_SWEEP_MIN_CALLS", "1e9")))
+    points = []
+    t_all = time.perf_counter()
+    with ClockSampler(local) as clocks:
+        for log2 in (24, 25, 26, 27, 28):
+            for lf in (0.5, 0.75, 0.9):
+                n_ids = int(lf * (1 << log2))
+                calls = 2 * n_ids
+                fills = max(1, -(-min_calls // calls))
+                tab = binding.Table(log2, 16)
+                for dist in ("uniform", "zipf"):
+                    zipf = synth.zipf_table(n_ids) if dist == "zipf" else None
+                    for mode in ("fused", "api"):
+                        keys = tab.gen_keys(1, n_ids, 0, calls, zipf) if mode == "api" else None
+
+                        def fill():
+                            tab.clear()
+                            if keys is None:
+                                tab.find_or_put_stream(1, n_ids, 0, calls, zipf, sync=False)
+                            else:
+                                tab.find_or_put(keys, want_idx=True)
+                        fill()
+                        torch.cuda.synchronize()
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        for _ in range(fills):
+                            fill()
+                        e1.record()
+                        torch.cuda.synchronize()
+                        ms = e0.elapsed_time(e1) / fills
+                        st = tab.stats()
+                        assert st.stored == n_ids and st.error == 0, (log2, lf, dist, mode)
+                        bound = hashtable_bound_s(calls, n_ids, rates, keys is not None)
+                        points.append({"log2_buckets": log2, "load_factor": lf, "dist": dist,
+                                       "keys": mode, "ops_per_s": calls / (ms / 1e3),
+                                       "ms_per_fill": ms, "timed_calls": calls * fills,
+                                       "random_roofline_frac": bound * 1e3 / ms})
+                        del keys
+                tab.close()
+                torch.cuda.empty_cache()
+    head = [p for p in points if p["log2_buckets"] == 26 and p["load_factor"] == 0.75
+            and p["dist"] == "uniform" and p["keys"] == "fused"][0]
+    line = base_line(args, world, "find_or_put ops/sec on 1 GB300 (hash-table benchmark sweep)",
+                     head["ops_per_s"], "find_or_put/s", head["ms_per_fill"],
+                     {"workload": "hashtable-sweep-W16-2^24..2^28-lf0.5,0.75,0.9-uniform,zipf-fused,api",
+                      "l2": "tables 1.1-18 GB, larger than L2", "min_timed_calls_per_point": min_calls})
+    line["points"] = points
+    line["sweep_seconds"] = time.perf_counter() - t_all
+    line["probe_rates_per_s"] = {"read32": rates[0], "read64": rates[1], "write32": rates[2],
+                                 "atomic32": rates[3]}
+    line["gpu_launches"] = sum(-(-min_calls // (2 * int(p["load_factor"] * (1 << p["log2_buckets"]))))
+                               for p in points)
+    line["clocks"] = clocks.summary()
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -72,7 +72,8 @@ enum {
 /* Tunable layout and safety limits; 0 in any field selects the default. */
 typedef struct {
   uint32_t line_buckets;  /* buckets walked per line before rehashing.  32-bit buckets:
-                             8, 16 or 32 (32, 64 or 128 bytes), default 8; 16-bit
+                             8, 16 or 32 (32, 64 or 128 bytes), default 32 (a
+                             128-byte line, read one 32-byte sector at a time); 16-bit
                              buckets: 16 or 32 (32 or 64 bytes), default 16 */
   uint32_t max_rehash;    /* lines probed before HT_ERR_FULL; default min(lines, 4096) */
   uint32_t max_spin;      /* polls of a write-busy bucket before HT_ERR_TIMEOUT; default 2^18 */
@@ -254,7 +255,7 @@ typedef struct {
 enum {
   REACH_PERSISTENT = 0, /* one cooperative launch runs every level (device-side level barrier) */
   REACH_PER_LEVEL = 1,  /* one launch per level; the host reads each level's size */
-  REACH_TRACE = 4       /* flag, with REACH_PERSISTENT and the default 8-bucket line: record
+  REACH_TRACE = 4       /* flag, with REACH_PERSISTENT and the default line length: record
                            predecessors so that reach_ctx_deadlock_trace can print a trace */
 };
 

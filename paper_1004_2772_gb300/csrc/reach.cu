@@ -440,7 +440,7 @@ ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
   if (mode == REACH_PERSISTENT) {
     if (!c->coop) return HT_ERR_CUDA;
     void (*kern)(TableView, ReachDev) = trace ? ks.persistent_trace : ks.persistent;
-    if (!kern) return HT_ERR_INVALID;  // tracing needs the default one-sector line
+    if (!kern) return HT_ERR_INVALID;  // tracing is compiled for the default line length
     VSS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));

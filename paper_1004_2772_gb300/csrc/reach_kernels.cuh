@@ -313,9 +313,9 @@ struct ReachKernels {
 
 template <int NV, int L, int BW>
 static ReachKernels kernels_for() {
-  // tracing is compiled for the default line of each bucket width only (one
-  // 32-byte sector: 8 buckets of 32 bits, 16 of 16 bits)
-  constexpr bool kTrace = (L * BW == 256);
+  // tracing is compiled for the default line of each bucket width only (32
+  // buckets of 32 bits, 16 of 16 bits)
+  constexpr bool kTrace = (BW == 32 ? L == 32 : L == 16);
   return {k_reach_persistent<NV, L, BW, false>,
           kTrace ? k_reach_persistent<NV, L, BW, kTrace> : nullptr, k_reach_seed<NV, L, BW>,
           k_reach_level<NV, L, BW>};

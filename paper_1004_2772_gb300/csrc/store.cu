@@ -264,7 +264,7 @@ ht_status resolve_params(const ht_params* in, uint64_t nb, ht_params* out) {
     if (p.line_buckets != 4 * G) return HT_ERR_INVALID;
   }
   if (p.bucket_bits == 32) {
-    if (p.line_buckets == 0) p.line_buckets = 8;
+    if (p.line_buckets == 0) p.line_buckets = 32;
     if (p.line_buckets != 8 && p.line_buckets != 16 && p.line_buckets != 32) return HT_ERR_INVALID;
   } else if (p.bucket_bits == 16) {
     if (p.line_buckets == 0) p.line_buckets = 16;

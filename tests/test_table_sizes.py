@@ -83,7 +83,7 @@ def test_buckets_for_bytes_is_largest_prime_line_table(L, W):
 def test_reach_ctx_buckets_for_bytes_fits():
     budget = 5 << 30
     nb = binding.reach_ctx_buckets_for_bytes(budget, 16, 4096)
-    assert _is_prime(nb // 8) and binding.reach_ctx_bytes_n(nb, 16, 4096) <= budget
+    assert _is_prime(nb // 32) and binding.reach_ctx_bytes_n(nb, 16, 4096) <= budget   # default 32-bucket lines
     assert binding.reach_ctx_bytes_n(nb, 16, 4096) > 0.95 * budget
 
 
@@ -134,7 +134,7 @@ def test_high_load_non_pow2(cuda_lib, lines):
     ids = np.repeat(np.arange(n_ids, dtype=np.uint64), 2)
     np.random.default_rng(lines).shuffle(ids)
     keys = synth.key_words(lines, ids, 16)
-    tab = cuda_lib.Table(None, 16, n_buckets=nb)
+    tab = cuda_lib.Table(None, 16, n_buckets=nb, line_buckets=8)
     seen, idx, cuts = run_batches(cuda_lib, tab, keys, 1)
     check_parity(tab, keys, seen, idx, cuts)
 
@@ -143,7 +143,7 @@ def test_high_load_non_pow2(cuda_lib, lines):
 def test_full_non_pow2_table_reports_full(cuda_lib):
     import torch
     keys = synth.key_words(9, np.arange(60, dtype=np.uint64), 16)
-    tab = cuda_lib.Table(None, 16, n_buckets=5 * 8)     # 5 lines of 8
+    tab = cuda_lib.Table(None, 16, n_buckets=5 * 8, line_buckets=8)     # 5 lines of 8
     s, _ = tab.find_or_put(torch.from_numpy(keys).cuda())
     torch.cuda.synchronize()
     s = s.cpu().numpy()
@@ -157,7 +157,7 @@ def test_fused_stream_non_pow2(cuda_lib):
     n_ids = 1 << 14
     ids = synth.call_ids(9, n_ids, 0, 2 * n_ids, "uniform")
     ref = oracle.find_or_put_stream(synth.key_words(9, ids, 16))
-    tab = cuda_lib.Table(None, 16, n_buckets=_prime_lines_near(40000 // 8) * 8)
+    tab = cuda_lib.Table(None, 16, n_buckets=_prime_lines_near(40000 // 32) * 32)  # default line
     n_new, dig = tab.find_or_put_stream(9, n_ids, 0, 2 * n_ids)
     assert (n_new, dig) == (ref.n_new, ref.digest)
 
@@ -167,10 +167,10 @@ def test_fused_stream_non_pow2(cuda_lib):
 def test_reach_non_pow2(cuda_lib, mode):
     from test_gpu_reach import check
     m = synth.tiny_interleaving_model()
-    ctx = cuda_lib.ReachContext(None, 5, max_levels=256, n_buckets=_prime_lines_near(150000 // 8) * 8)
+    ctx = cuda_lib.ReachContext(None, 5, max_levels=256, n_buckets=_prime_lines_near(150000 // 32) * 32)
     got = check(cuda_lib, ctx, m, mode)
     assert got.states == 100000
-    ctx2 = cuda_lib.ReachContext(None, 8, max_levels=64, n_buckets=13 * 8)
+    ctx2 = cuda_lib.ReachContext(None, 8, max_levels=64, n_buckets=13 * 8, line_buckets=8)
     for hm, d in hand_models():
         check(cuda_lib, ctx2, hm, mode)
 
@@ -179,7 +179,7 @@ def test_reach_non_pow2(cuda_lib, mode):
 def test_beem_shaped_medium_non_pow2(cuda_lib):
     g = load_golden("beem_medium.json")
     m = synth.beem_shaped_model(**g["model"])
-    nb = _prime_lines_near(int(1.5 * g["states"]) // 8) * 8          # load factor ~0.67
+    nb = _prime_lines_near(int(1.5 * g["states"]) // 32) * 32        # load factor ~0.67
     ctx = cuda_lib.ReachContext(None, 16, max_levels=4096, n_buckets=nb)
     for mode in (0, 1):
         got = ctx.reach(m, mode=mode)
