@@ -1,6 +1,5 @@
 """The autotuner: its search space (host logic, no GPU) and, on the GPU, that
 every candidate of a tuning run reproduces the oracle's answer."""
-import numpy as np
 import pytest
 
 import oracle

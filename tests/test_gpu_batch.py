@@ -5,7 +5,6 @@ that model alone: states, transitions, deadlocks, level sizes and digest --
 whatever the interleaving with the other models, whether tables had to grow,
 and whether the batch ran as a plain launch or as a replayed CUDA graph.
 """
-import numpy as np
 import pytest
 
 import oracle
