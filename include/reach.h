@@ -180,9 +180,9 @@ ht_status ht_scan(ht_t* h, void* stream, uint64_t* done, uint64_t* writing, uint
 /* Copy rows idx_dev[0..n) of the data array to out_dev (n x state_words int32). */
 ht_status ht_gather(ht_t* h, const uint32_t* idx_dev, uint64_t n, int32_t* out_dev, void* stream);
 
-/* Device pointers to the bucket array (2^log2_buckets words of bucket_bits
- * bits: uint32 or uint16) and data array (rows of 4*ceil(state_words/4) int32),
- * for inspection. */
+/* Device pointers to the bucket array (one word of bucket_bits bits, uint32 or
+ * uint16, per bucket: 2^log2_buckets or n_buckets of them) and data array
+ * (rows of 4*ceil(state_words/4) int32), for inspection. */
 ht_status ht_arrays(ht_t* h, uint32_t** buckets_dev, int32_t** data_dev, uint32_t* row_words);
 
 /* ------------------------------------------------------------------------ */
