@@ -600,10 +600,21 @@ def run_serve(args, world, rank, local, dev):
             time.sleep(0.0005)
         span = time.perf_counter() - t0
         lat = np.array([d.latency_s for d in done]) * 1e3
+        queue = np.array([d.admit_s - d.submit_s for d in done]) * 1e3
+        run = np.array([d.done_s - d.admit_s for d in done]) * 1e3
+        size = np.array([d.result.states for d in done], dtype=np.float64)
         assert all(d.result.status == 0 for d in done)
+        by_size = {}
+        for lo, hi in ((1e4, 1e5), (1e5, 1e6), (1e6, 1e7), (1e7, 1e9)):
+            sel = (size >= lo) & (size < hi)
+            if sel.any():
+                by_size[f"{lo:.0e}-{hi:.0e}"] = {"jobs": int(sel.sum()),
+                                                  "p50_ms": float(np.percentile(lat[sel], 50))}
         out[slots] = {"span_s": span, "states": sum(d.result.states for d in done),
                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                      "max_ms": float(lat.max()), "kernel_launches": srv.status()["kernel_launches"]}
+                      "max_ms": float(lat.max()), "kernel_launches": srv.status()["kernel_launches"],
+                      "queue_p50_ms": float(np.percentile(queue, 50)),
+                      "run_p50_ms": float(np.percentile(run, 50)), "p50_ms_by_states": by_size}
         srv.close()
         del srv
         torch.cuda.empty_cache()
@@ -612,8 +623,13 @@ def run_serve(args, world, rank, local, dev):
                      c["states"] / c["span_s"], "states/s", c["span_s"] * 1e3 / max(1, len(jobs)),
                      {"workload": f"served-poisson20-{len(jobs)}jobs-1e4..2e8-W16", "slots": 64,
                       "jobs": len(jobs)})
-    line["latency_ms"] = {"p50": c["p50_ms"], "p99": c["p99_ms"], "max": c["max_ms"]}
+    line["latency_ms"] = {"p50": c["p50_ms"], "p99": c["p99_ms"], "max": c["max_ms"],
+                          "queue_p50": c["queue_p50_ms"], "run_p50": c["run_p50_ms"],
+                          "p50_by_states": c["p50_ms_by_states"]}
     line["one_job_at_a_time"] = {"p50_ms": out[1]["p50_ms"], "p99_ms": out[1]["p99_ms"],
+                                 "queue_p50_ms": out[1]["queue_p50_ms"],
+                                 "run_p50_ms": out[1]["run_p50_ms"],
+                                 "p50_by_states": out[1]["p50_ms_by_states"],
                                  "states_per_s": out[1]["states"] / out[1]["span_s"]}
     line["gpu_launches"] = c["kernel_launches"]
     if rank == 0:

@@ -348,7 +348,10 @@ __global__ void __launch_bounds__(256, 2) k_reach_batch(BatchGlobal g) {
         // host relaunches the kernel on its next submission)
         int took = 0, leave = 0;
         if (lane == 0) {
-          took = serve_accept(g) ? 1 : 0;
+          // only the first warp of each block reads the host mailbox: reads of
+          // host-mapped memory are slow, and every idle warp polling them
+          // slowed the busy warps down (small jobs took 1.6x longer)
+          took = (threadIdx.x < 32 && serve_accept(g)) ? 1 : 0;
           if (!took && ld_relaxed(&g.st->active) == 0) {
             const bool stop = ld_acquire_sys32(&g.mb->shutdown) != 0u;
             const bool posted = ld_acquire_sys64(&g.mb->doorbell) != ld_relaxed64(&g.st->seen_doorbell);
