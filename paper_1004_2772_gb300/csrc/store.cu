@@ -477,7 +477,9 @@ ht_status ht_find_or_put(ht_t* h, const int32_t* keys_dev, uint64_t n, uint8_t* 
   if (n == 0) return HT_OK;
   const int threads = (int)h->params.block_threads;
   const uint64_t want = (n * h->params.group_lanes + threads - 1) / threads;  // G lanes per key
-  const uint64_t cap = (uint64_t)h->num_sms * 16;
+  // 64 blocks per SM, run in waves: measured 6-26 % faster than 16 (the
+  // grid-stride loop of fewer, longer-lived blocks ends unevenly)
+  const uint64_t cap = (uint64_t)h->num_sms * 64;
   const int blocks = (int)(want < cap ? want : cap);
   FopKernel k = pick_fop((int)h->view.nv, (int)h->params.line_buckets, (int)h->view.bucket_bits,
                          h->params.dedup != 0, (int)h->params.group_lanes);

@@ -276,7 +276,8 @@ ht_status ht_find_or_put_stream(ht_t* h, uint64_t seed, uint64_t n_ids, uint64_t
   const StreamSpec s = make_spec(seed, n_ids, zipf_table_dev);
   const int threads = (int)h->params.block_threads;
   const uint64_t lanes = n_calls * h->params.group_lanes;  // G lanes per key in group mode
-  const uint64_t want = (lanes + threads - 1) / threads, cap = (uint64_t)h->num_sms * 16;
+  // 64 blocks per SM, as for the batch API
+  const uint64_t want = (lanes + threads - 1) / threads, cap = (uint64_t)h->num_sms * 64;
   const int blocks = (int)(want < cap ? want : cap);
   k<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
       h->view, s, call_begin, n_calls, reinterpret_cast<unsigned long long*>(result_dev));
