@@ -386,7 +386,13 @@ __global__ void __launch_bounds__(256, 2) k_reach_batch(BatchGlobal g) {
     if (lane == 0) {
       const unsigned long long w = ld_relaxed64(&M.claim);
       if (cl_phase(w) == PH_EXPAND) {
-        take = cl_units(w) >> 6;
+        // the model's fair share of the grid: its level spread over
+        // warps / active models, so that a lone model's level takes one short
+        // round on every warp while many models keep claims large
+        const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+        uint32_t active = g.mb ? ld_relaxed(&g.st->active) : g.n_models - ld_relaxed(&g.st->finished);
+        active = active < 1u ? 1u : active;
+        take = (uint32_t)(((uint64_t)cl_units(w) * active + warps - 1) / warps);
         take = take < 1u ? 1u : (take > M.spw_max ? M.spw_max : take);
       }
       const unsigned long long old = atom_add_acqrel64(&M.claim, take);
