@@ -31,6 +31,27 @@ ht_status table_init_at(ht_t* h, uint64_t nb, int max_words, const ht_params* pa
 uint64_t prime_line_buckets(uint64_t max_nb, uint32_t line_buckets);
 ht_status table_set_words(ht_t* h, int words);
 ht_status table_clear(ht_t* h, cudaStream_t s);
+// A single-model run on device areas the caller carved (the server's path for
+// a job that arrives at an idle GPU): table view (power of two), packed model,
+// two frontiers of cap rows, run totals (solo_totals_bytes()), per-level sizes
+// and start times of max_levels entries.  solo_launch clears the table and the
+// totals and launches the persistent kernel on s; solo_result reads the result
+// once s has finished it (synchronous copies).
+struct SoloRun {
+  TableView tv;
+  const int* blob_dev;
+  int smem_words;
+  uint4* fr0;
+  uint4* fr1;
+  uint32_t cap;
+  void* tot_dev;
+  unsigned long long* level_sizes_dev;
+  unsigned long long* level_ns_dev;
+  uint32_t max_levels;
+};
+uint64_t solo_totals_bytes();
+ht_status solo_launch(const SoloRun& r, int line_buckets, int threads, cudaStream_t s);
+ht_status solo_result(const SoloRun& r, reach_result* out);
 // Validate a model and pack it (with init) into the device blob format;
 // blob header word [k]: see reach.cu.
 ht_status pack_model(const reach_model* m, const int32_t* init, int max_words,

@@ -690,3 +690,71 @@ extern "C" ht_status reach_noalloc(const reach_model* m, const int32_t* init_hos
   }
   return out->status;
 }
+
+// ---------------------------------------------------------------------------
+// One single-model run on device areas carved by the caller: the server runs a
+// job that arrives at an idle GPU this way (the persistent single-model kernel
+// has a shorter level path than the many-model kernel).
+// ---------------------------------------------------------------------------
+namespace vss {
+
+uint64_t solo_totals_bytes() { return sizeof(ReachTotals); }
+
+ht_status solo_launch(const SoloRun& r, int line_buckets, int threads, cudaStream_t s) {
+  const uint32_t nv = r.tv.nv;
+  const ReachKernels ks = pick_kernels((int)nv, line_buckets, (int)r.tv.bucket_bits);
+  if (!ks.persistent || r.tv.lines_div.m != 0) return HT_ERR_INVALID;  // power-of-two tables
+  const uint64_t nb = (uint64_t)r.tv.nb_mask + 1;
+  VSS_CUDA_TRY(cudaMemsetAsync(r.tv.ctr, 0, sizeof(DevCounters), s));
+  VSS_CUDA_TRY(cudaMemsetAsync(r.tv.buckets, 0, nb * (r.tv.bucket_bits / 8), s));
+  ReachTotals* tot = static_cast<ReachTotals*>(r.tot_dev);
+  VSS_CUDA_TRY(cudaMemsetAsync(tot, 0, sizeof(ReachTotals), s));
+  VSS_CUDA_TRY(cudaMemsetAsync(&tot->first_deadlock, 0xFF, sizeof(unsigned long long), s));
+  const size_t smem = (size_t)((r.smem_words + 3) & ~3) * 4 +
+                      (size_t)(threads / 32) * warp_smem_words_nv((int)nv) * 4;
+  if (smem > 200 * 1024) return HT_ERR_INVALID;
+  int dev = 0, sms = 0, coop = 0, per_sm = 0;
+  VSS_CUDA_TRY(cudaGetDevice(&dev));
+  VSS_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  VSS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (!coop) return HT_ERR_CUDA;
+  VSS_CUDA_TRY(cudaFuncSetAttribute(ks.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.persistent, threads, smem));
+  if (per_sm < 1) return HT_ERR_INVALID;
+  TableView tv = r.tv;
+  ReachDev rd{};
+  rd.blob = r.blob_dev;
+  rd.smem_words = r.smem_words;
+  rd.frontier0 = r.fr0;
+  rd.frontier1 = r.fr1;
+  rd.cap = r.cap;
+  rd.tot = tot;
+  rd.level_sizes = r.level_sizes_dev;
+  rd.level_ns = r.level_ns_dev;
+  rd.max_levels = r.max_levels;
+  rd.bar_spin = 1u << 22;
+  void* args[] = {&tv, &rd};
+  VSS_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(ks.persistent), per_sm * sms,
+                                           threads, args, smem, s));
+  return HT_OK;
+}
+
+ht_status solo_result(const SoloRun& r, reach_result* out) {
+  std::memset(out, 0, sizeof(*out));
+  ReachTotals t;
+  DevCounters ctr;
+  VSS_CUDA_TRY(cudaMemcpy(&t, r.tot_dev, sizeof(t), cudaMemcpyDeviceToHost));
+  VSS_CUDA_TRY(cudaMemcpy(&ctr, r.tv.ctr, sizeof(ctr), cudaMemcpyDeviceToHost));
+  out->transitions = t.transitions;
+  out->deadlocks = t.deadlocks;
+  out->digest = t.digest;
+  out->states = ctr.stored;
+  out->busy_waits = ctr.busy_waits;
+  out->rehashes = ctr.rehashes;
+  out->n_levels = t.n_levels;
+  out->status = (ht_status)ctr.err;
+  return out->status;
+}
+
+}  // namespace vss

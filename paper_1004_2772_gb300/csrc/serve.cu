@@ -11,6 +11,12 @@
 // memory, which may admit the next queued job.  The kernel leaves on its own
 // once nothing has run for a while (every wait on the device is bounded), and
 // the host relaunches it on the next submission.
+//
+// A job that arrives at an idle GPU (no job running, none queued, the
+// many-job kernel gone) runs alone on the persistent single-model kernel,
+// whose level path is shorter; jobs that arrive meanwhile queue, and when it
+// is done the queue goes to the many-job kernel (or, if it holds one job, to
+// another single run).  Both run on the same stream, so they never overlap.
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -89,6 +95,7 @@ struct serve {
   ServeSlotOut* out = nullptr;
   struct Slot {
     bool busy = false;
+    bool solo = false;  // running on the single-model kernel, not in the many-job kernel
     uint64_t job = 0, seq = 0, off = 0, bytes = 0;
     double t_submit = 0, t_admit = 0;
   };
@@ -100,6 +107,7 @@ struct serve {
     int log2;
     unsigned long long bound;
     double t_submit;
+    bool no_solo = false;  // the single-model kernel cannot take it (e.g. shared memory)
   };
   std::deque<Job> pending;
   std::vector<serve_done_t> rejected;  // jobs that can never fit, reported by the next poll
@@ -111,11 +119,79 @@ struct serve {
   size_t smem = 0;
   bool launched = false;
   uint64_t launches = 0;
+  // single-model path
+  bool solo = false;  // a single-model run is in flight on kstream
+  uint32_t solo_slot = 0;
+  SoloRun solo_run{};
+  void* solo_tot_dev = nullptr;
+  unsigned long long* solo_ns_dev = nullptr;
+  cudaEvent_t solo_ev = nullptr;
 };
 
 static uint64_t serve_fixed_bytes(uint32_t n_slots, uint32_t max_levels) {
   return up256((uint64_t)n_slots * sizeof(BatchModel)) + up256(sizeof(BatchState)) +
-         up256((uint64_t)n_slots * 8) + up256((uint64_t)n_slots * max_levels * 8);
+         up256((uint64_t)n_slots * 8) + up256((uint64_t)n_slots * max_levels * 8) +
+         up256(solo_totals_bytes()) + up256((uint64_t)max_levels * 8);
+}
+
+static bool batch_busy(const serve_t* s) {
+  for (auto& sl : s->slots)
+    if (sl.busy && !sl.solo) return true;
+  return false;
+}
+
+// Start the front job alone on the single-model kernel.  Returns false when
+// it cannot (the job then goes to the many-job kernel).
+static bool start_solo(serve_t* s, uint32_t slot, uint64_t off, uint64_t bytes, uint64_t blob_bytes) {
+  serve_t::Job& job = s->pending.front();
+  const uint32_t nv = (job.W + 3) / 4;
+  const uint64_t nb = 1ull << job.log2;
+  const uint32_t L = s->params.line_buckets;
+  char* base = s->arena_dev + off;
+  char* gp = base + blob_bytes;
+  SoloRun& r = s->solo_run;
+  r = SoloRun{};
+  r.tv.buckets = reinterpret_cast<uint32_t*>(gp);
+  r.tv.data = reinterpret_cast<uint4*>(gp + up256(nb * 4));
+  r.tv.ctr = &s->slots_dev[slot].ctr;
+  r.tv.seed = s->g.seed;
+  r.tv.nb_mask = (uint32_t)(nb - 1);
+  r.tv.lines = (uint32_t)(nb / L);
+  r.tv.lines_mask = r.tv.lines - 1;
+  r.tv.lines_div = DivU64{0, 0, 0};
+  r.tv.max_rehash = r.tv.lines < 4096u ? r.tv.lines : 4096u;
+  r.tv.max_spin = s->params.max_spin;
+  r.tv.state_words = job.W;
+  r.tv.nv = nv;
+  r.tv.bucket_bits = 32;
+  r.blob_dev = reinterpret_cast<const int*>(base);
+  r.smem_words = job.blob[11];
+  r.fr0 = reinterpret_cast<uint4*>(gp + up256(nb * 4) + up256(nb * 16 * nv));
+  r.fr1 = reinterpret_cast<uint4*>(gp + up256(nb * 4) + 2 * up256(nb * 16 * nv));
+  r.cap = (uint32_t)nb;
+  r.tot_dev = s->solo_tot_dev;
+  r.level_sizes_dev = s->levels_dev + (uint64_t)slot * s->max_levels;
+  r.level_ns_dev = s->solo_ns_dev;
+  r.max_levels = s->max_levels;
+  if (solo_launch(r, (int)L, (int)s->params.block_threads, s->kstream) != HT_OK ||
+      cudaEventRecord(s->solo_ev, s->kstream) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  serve_t::Slot& sl = s->slots[slot];
+  sl.busy = true;
+  sl.solo = true;
+  sl.job = job.id;
+  sl.seq = 0;
+  sl.off = off;
+  sl.bytes = bytes;
+  sl.t_submit = job.t_submit;
+  sl.t_admit = now_s();
+  s->solo = true;
+  s->solo_slot = slot;
+  s->launches++;
+  s->pending.pop_front();
+  return true;
 }
 
 static ht_status ensure_running(serve_t* s) {
@@ -132,6 +208,7 @@ static ht_status ensure_running(serve_t* s) {
 }
 
 static void admit(serve_t* s) {
+  if (s->solo) return;  // queued jobs wait for the single-model run
   while (!s->pending.empty()) {
     uint32_t slot = s->n_slots;
     bool any_busy = false;
@@ -168,6 +245,13 @@ static void admit(serve_t* s) {
       cudaGetLastError();
       s->arena.release(off, bytes);
       return;
+    }
+    // an idle GPU and a lone job: run it on the single-model kernel
+    const bool gpu_idle = !any_busy && s->pending.size() == 1 &&
+                          (!s->launched || cudaStreamQuery(s->kstream) == cudaSuccess);
+    if (gpu_idle && !job.no_solo) {
+      if (start_solo(s, slot, off, bytes, blob_bytes)) return;
+      job.no_solo = true;
     }
     const uint64_t nb = 1ull << job.log2;
     char* gp = base + blob_bytes;
@@ -244,6 +328,10 @@ ht_status serve_open_at(void* mem_dev, uint64_t mem_bytes, uint32_t n_slots, uin
   q += up256((uint64_t)n_slots * 8);
   s->levels_dev = reinterpret_cast<unsigned long long*>(q);
   q += up256((uint64_t)n_slots * max_levels * 8);
+  s->solo_tot_dev = q;
+  q += up256(solo_totals_bytes());
+  s->solo_ns_dev = reinterpret_cast<unsigned long long*>(q);
+  q += up256((uint64_t)max_levels * 8);
   s->arena_dev = q;
   s->arena.init((mem_bytes - fixed) & ~255ull);
   s->slots.resize(n_slots);
@@ -254,6 +342,7 @@ ht_status serve_open_at(void* mem_dev, uint64_t mem_bytes, uint32_t n_slots, uin
     if (s->out) cudaFreeHost(s->out);
     if (s->kstream) cudaStreamDestroy(s->kstream);
     if (s->cstream) cudaStreamDestroy(s->cstream);
+    if (s->solo_ev) cudaEventDestroy(s->solo_ev);
     cudaGetLastError();
     delete s;
     return code;
@@ -262,7 +351,8 @@ ht_status serve_open_at(void* mem_dev, uint64_t mem_bytes, uint32_t n_slots, uin
       cudaHostAlloc(reinterpret_cast<void**>(&s->in), sizeof(ServeSlotIn) * n_slots, cudaHostAllocMapped) != cudaSuccess ||
       cudaHostAlloc(reinterpret_cast<void**>(&s->out), sizeof(ServeSlotOut) * n_slots, cudaHostAllocMapped) != cudaSuccess ||
       cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess)
+      cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->solo_ev, cudaEventDisableTiming) != cudaSuccess)
     return fail(HT_ERR_CUDA);
   std::memset(s->mb, 0, sizeof(ServeMailbox));
   std::memset(s->in, 0, sizeof(ServeSlotIn) * n_slots);
@@ -300,7 +390,8 @@ ht_status serve_open_at(void* mem_dev, uint64_t mem_bytes, uint32_t n_slots, uin
   g.seed = p.hash_seed;
   g.n_models = n_slots;
   g.max_spin = p.max_spin;
-  g.idle_ns = 100000000ull;    // 0.1 s without any work: the kernel leaves
+  g.idle_ns = 2000000ull;      // 2 ms without any work: the kernel leaves (and the next
+                               // job to arrive at the idle GPU runs on the single-model kernel)
   g.stuck_ns = 4000000000ull;  // 4 s with jobs in slots but nothing claimable: error
   g.grow_at = 0.9f;
   g.grow_to = 0.5f;
@@ -358,9 +449,7 @@ ht_status serve_submit(serve_t* s, const reach_model* m, const int32_t* init_hos
   if (job_id) *job_id = job.id;
   s->pending.push_back(std::move(job));
   admit(s);
-  bool busy = false;
-  for (auto& sl : s->slots) busy |= sl.busy;
-  return busy ? ensure_running(s) : HT_OK;
+  return batch_busy(s) ? ensure_running(s) : HT_OK;
 }
 
 ht_status serve_poll(serve_t* s, serve_done_t* done, uint32_t max_done, uint32_t* n_done,
@@ -371,9 +460,33 @@ ht_status serve_poll(serve_t* s, serve_done_t* done, uint32_t max_done, uint32_t
     done[n++] = s->rejected.back();
     s->rejected.pop_back();
   }
+  if (s->solo && n < max_done) {
+    const cudaError_t q = cudaEventQuery(s->solo_ev);
+    if (q != cudaSuccess && q != cudaErrorNotReady) return HT_ERR_CUDA;
+    if (q == cudaSuccess) {
+      serve_t::Slot& sl = s->slots[s->solo_slot];
+      serve_done_t& d = done[n];
+      std::memset(&d, 0, sizeof(d));
+      d.job_id = sl.job;
+      solo_result(s->solo_run, &d.result);
+      d.submit_s = sl.t_submit;
+      d.admit_s = sl.t_admit;
+      d.done_s = now_s();
+      if (level_sizes_host && d.result.n_levels) {
+        const uint32_t nl = d.result.n_levels < s->max_levels ? d.result.n_levels : s->max_levels;
+        VSS_CUDA_TRY(cudaMemcpy(level_sizes_host + (uint64_t)n * s->max_levels,
+                                s->solo_run.level_sizes_dev, (size_t)nl * 8, cudaMemcpyDeviceToHost));
+      }
+      s->arena.release(sl.off, sl.bytes);
+      sl.busy = false;
+      sl.solo = false;
+      s->solo = false;
+      ++n;
+    }
+  }
   for (uint32_t i = 0; i < s->n_slots && n < max_done; ++i) {
     serve_t::Slot& sl = s->slots[i];
-    if (!sl.busy) continue;
+    if (!sl.busy || sl.solo) continue;
     if (__atomic_load_n(&s->out[i].seq, __ATOMIC_ACQUIRE) != sl.seq) continue;
     const ServeSlotOut& o = s->out[i];
     serve_done_t& d = done[n];
@@ -404,9 +517,7 @@ ht_status serve_poll(serve_t* s, serve_done_t* done, uint32_t max_done, uint32_t
   }
   *n_done = n;
   admit(s);
-  bool busy = false;
-  for (auto& sl : s->slots) busy |= sl.busy;
-  if (busy) {
+  if (batch_busy(s)) {
     // a kernel that stopped with jobs still in their slots hit a device error
     if (s->launched && cudaStreamQuery(s->kstream) == cudaSuccess) {
       BatchState bst;
@@ -441,6 +552,7 @@ ht_status serve_close(serve_t* s) {
   if (s->launched && cudaStreamSynchronize(s->kstream) != cudaSuccess) st = HT_ERR_CUDA;
   cudaStreamDestroy(s->kstream);
   cudaStreamDestroy(s->cstream);
+  cudaEventDestroy(s->solo_ev);
   cudaFreeHost(s->mb);
   cudaFreeHost(s->in);
   cudaFreeHost(s->out);
