@@ -95,55 +95,6 @@ __device__ __forceinline__ void st_v8(void* p, const uint4& a, const uint4& b) {
                : "memory");
 }
 
-// L2 eviction-priority hints (0 = none, the default):
-//   VSS_FRONTIER_HINT 1  frontier rows are read and written L2::evict_first
-//                        (each is touched once per level);
-//   VSS_BUCKET_HINT 1    bucket sectors are read L2::evict_last;
-//   VSS_DATA_HINT 1      data rows are written L2::evict_last on insert.
-#ifndef VSS_FRONTIER_HINT
-#define VSS_FRONTIER_HINT 0
-#endif
-#ifndef VSS_BUCKET_HINT
-#define VSS_BUCKET_HINT 0
-#endif
-#ifndef VSS_DATA_HINT
-#define VSS_DATA_HINT 0
-#endif
-
-__device__ __forceinline__ void ld_front_v8(const void* p, uint4& a, uint4& b) {
-#if VSS_FRONTIER_HINT
-  asm volatile("ld.relaxed.gpu.global.L2::evict_first.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : VSS_V8_OUT(a, b) : "l"(p) : "memory");
-#else
-  ld_cg_v8(p, a, b);
-#endif
-}
-__device__ __forceinline__ void st_front_v8(void* p, const uint4& a, const uint4& b) {
-#if VSS_FRONTIER_HINT
-  asm volatile("st.global.L1::no_allocate.L2::evict_first.v8.u32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
-               ::"l"(p), "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
-               : "memory");
-#else
-  st_v8(p, a, b);
-#endif
-}
-__device__ __forceinline__ void st_data_v8(void* p, const uint4& a, const uint4& b) {
-#if VSS_DATA_HINT
-  asm volatile("st.global.L2::evict_last.v8.u32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p),
-               "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
-               : "memory");
-#else
-  st_v8(p, a, b);
-#endif
-}
-__device__ __forceinline__ void ld_acquire_bucket_v8(const void* p, uint4& a, uint4& b) {
-#if VSS_BUCKET_HINT
-  asm volatile("ld.acquire.gpu.global.L2::evict_last.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : VSS_V8_OUT(a, b) : "l"(p) : "memory");
-#else
-  ld_acquire_v8(p, a, b);
-#endif
-}
 #undef VSS_V8_OUT
 
 __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
@@ -368,29 +319,7 @@ template <int NV>
 __device__ __forceinline__ void store_row(uint4* row, const Vec<NV>& v) {
   if (NV % 2 == 0) {
 #pragma unroll
-    for (int j = 0; j < NV; j += 2) st_data_v8(row + j, v.c[j], v.c[(j + 1) % NV]);
-  } else {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) row[j] = v.c[j];
-  }
-}
-
-// Frontier rows: read once and written once per level.
-template <int NV>
-__device__ __forceinline__ void load_front(const uint4* row, Vec<NV>& v) {
-  if (NV % 2 == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; j += 2) ld_front_v8(row + j, v.c[j], v.c[(j + 1) % NV]);
-  } else {
-#pragma unroll
-    for (int j = 0; j < NV; ++j) v.c[j] = __ldcg(row + j);
-  }
-}
-template <int NV>
-__device__ __forceinline__ void store_front(uint4* row, const Vec<NV>& v) {
-  if (NV % 2 == 0) {
-#pragma unroll
-    for (int j = 0; j < NV; j += 2) st_front_v8(row + j, v.c[j], v.c[(j + 1) % NV]);
+    for (int j = 0; j < NV; j += 2) st_v8(row + j, v.c[j], v.c[(j + 1) % NV]);
   } else {
 #pragma unroll
     for (int j = 0; j < NV; ++j) row[j] = v.c[j];

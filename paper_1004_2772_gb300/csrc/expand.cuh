@@ -96,7 +96,7 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
     uint4* r = reinterpret_cast<uint4*>(rows + lane * RS);
     Vec<NV> v;
     if (RT) load_row_cg_rt<NV>(cur + f * nvr, v, nvr);
-    else load_front<NV>(cur + f * NV, v);
+    else load_row_cg<NV>(cur + f * NV, v);
 #pragma unroll
     for (int j = 0; j < NV; ++j) r[j] = v.c[j];
     // the parent's hash sum, kept in the row's padding for its successors
@@ -239,7 +239,7 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
         const uint32_t pos = wbase + __popc(nb & ((1u << lane) - 1u));
         if (pos < cap) {
           if (RT) store_row_rt<NV>(next + (size_t)pos * nvr, w, nvr);
-          else store_front<NV>(next + (size_t)pos * NV, w);
+          else store_row<NV>(next + (size_t)pos * NV, w);
           if (TR) tr->next_idx[pos] = new_idx;
         } else {
           latch_error(t.ctr, HT_ERR_FULL);

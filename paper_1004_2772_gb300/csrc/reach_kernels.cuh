@@ -15,9 +15,6 @@ namespace vss {
 #ifndef VSS_BARRIER_STATS
 #define VSS_BARRIER_STATS 0  // measurement builds only: record barrier arrival spreads
 #endif
-#ifndef VSS_GUIDED
-#define VSS_GUIDED 0  // F > 0: a dynamic claim takes ceil(left / (F * warps)) states (at most spw)
-#endif
 #ifndef VSS_REACH_MINB
 #define VSS_REACH_MINB 3  // __launch_bounds__ minimum resident blocks of the expansion kernels
 #endif             // successor descriptors per warp and round
@@ -104,36 +101,23 @@ __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, c
   spw = spw < 1u ? 1u : (spw > (uint32_t)m.spw_max ? (uint32_t)m.spw_max : spw);
   const uint32_t warp_id = blockIdx.x * wpb + (threadIdx.x >> 5);
   const uint64_t static_rows = (uint64_t)warps * spw;
-  uint32_t claim = spw;  // states per dynamic claim
   for (bool first = true;; first = false) {
     // the first round is static (warp w takes rows w*spw ..); later rounds are
     // claimed from the level cursor, so warps that finish early take more,
     // and a level that fits in one round costs no atomic at all
     uint64_t base = (uint64_t)warp_id * spw;
-    uint32_t count = spw;
     if (!first) {
       if (static_rows >= n_cur) break;
       uint32_t c0 = 0;
-      if (lane == 0) c0 = atomicAdd(cursor, claim);
-      c0 = __shfl_sync(0xffffffffu, c0, 0);
-      base = static_rows + c0;
-      count = claim;
-#if VSS_GUIDED
-      // guided self-scheduling: claims shrink with the work left, so the
-      // level ends with short rounds instead of one full round per warp
-      const uint64_t dyn = n_cur - static_rows, taken = (uint64_t)c0 + claim;
-      const uint64_t left = dyn > taken ? dyn - taken : 0;
-      const uint64_t share = (uint64_t)VSS_GUIDED * warps;
-      const uint64_t want = (left + share - 1) / share;
-      claim = want < 1 ? 1u : (want > spw ? spw : (uint32_t)want);
-#endif
+      if (lane == 0) c0 = atomicAdd(cursor, spw);
+      base = static_rows + __shfl_sync(0xffffffffu, c0, 0);
     }
     if (base >= n_cur) {
       if (first) continue;
       break;
     }
-    expand_round<NV, L, false, TR, BW>(t, m, cur, n_cur, base, count, next, next_count, cap, acc,
-                                       lc, wsm, tr);
+    expand_round<NV, L, false, TR, BW>(t, m, cur, n_cur, base, spw, next, next_count, cap, acc, lc,
+                                       wsm, tr);
   }
 }
 

@@ -43,7 +43,7 @@ namespace vss {
 // One 32-byte bucket sector in one instruction.
 __device__ __forceinline__ void ld_sector(const uint32_t* p, uint4& a, uint4& b) {
 #if VSS_ACQ_MODE == 1
-  ld_acquire_bucket_v8(p, a, b);
+  ld_acquire_v8(p, a, b);
 #else
   ld_relaxed_v8(p, a, b);
 #endif
