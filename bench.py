@@ -51,7 +51,7 @@ MAX_LEVELS = 1 << 14
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_reach_persistent launch on
 # the full BEEM-shaped workload (ncu, 1 pass; profiles/k_reach_persistent_beem-shaped.md).
 # Must be re-measured (or set to None) whenever the kernel changes.
-NCU_TRAFFIC_BYTES = {"beem": 24.12e9}
+NCU_TRAFFIC_BYTES = {"beem": 24.08e9}
 
 
 def workload_model(name="beem"):
