@@ -96,3 +96,29 @@ def test_staggered_arrivals_and_kernel_restart(cuda_lib, jobs):
         _same(got[jid].result, ref)
     assert srv.status()["kernel_launches"] >= 2
     srv.close()
+
+
+def test_lone_jobs_on_idle_server_guarded_and_full(cuda_lib):
+    """Jobs that find the GPU idle run on the single-model kernel: a guarded
+    model (shared variables, table size given), a table too small for its job
+    (HT_ERR_FULL, the server keeps serving), then a burst that goes to the
+    many-job kernel."""
+    from test_oracle_pins import TINY_BEEM
+    srv = cuda_lib.Server(budget_bytes=1 << 30, n_slots=4, max_levels=2048)
+    guarded = synth.beem_shaped_model(**TINY_BEEM[0])
+    ref = oracle.reach(guarded)
+    jid = srv.submit(guarded, log2_buckets=14)
+    got = _drain(srv, 1)
+    _same(got[jid].result, ref)
+    small = synth.sized_interleaving_model(7, 4, 16, 20000)        # 20k states into 2^10 buckets
+    jid = srv.submit(small, log2_buckets=10)
+    got = _drain(srv, 1)
+    assert got[jid].result.status == cuda_lib.HT_ERR_FULL
+    burst = [synth.sized_interleaving_model(100 + k, 3 + k % 4, 16, 3000 + 700 * k) for k in range(6)]
+    refs = [oracle.reach(m) for m in burst]
+    ids = [srv.submit(m) for m in burst]
+    got = _drain(srv, len(ids))
+    for i, r in zip(ids, refs):
+        _same(got[i].result, r)
+    assert srv.status()["kernel_launches"] >= 3
+    srv.close()
