@@ -401,11 +401,11 @@ ht_status reach_batch_last_timing(reach_batch_t* b, float* ms);
  * finished job is returned by serve_poll and its memory freed, which may admit
  * queued jobs.  Each job's result equals reach() on it alone.  The kernel
  * leaves after ~2 ms without work (all device waits are bounded) and is
- * relaunched by the next submit or poll.  A job that finds the GPU idle (no
- * job running or queued, the kernel gone) runs alone on the single-model
- * persistent kernel of reach() instead, on the same stream; jobs submitted
- * meanwhile queue until it is done.  serve_status counts both kinds of
- * launch.  One host thread at a time. */
+ * relaunched by the next submit or poll.  While fewer than 8 jobs wait and
+ * the kernel is gone, jobs run one at a time on the single-model persistent
+ * kernel of reach() instead, on the same stream (jobs submitted meanwhile
+ * queue); 8 or more waiting jobs go to the many-job kernel together.
+ * serve_status counts both kinds of launch.  One host thread at a time. */
 typedef struct serve serve_t;
 
 typedef struct {
