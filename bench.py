@@ -245,7 +245,7 @@ def main():
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="persistent", choices=["persistent", "per-level"])
+    ap.add_argument("--mode", default="persistent", choices=["persistent", "per-level", "graph"])
     ap.add_argument("--line-buckets", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="beem", choices=sorted(WORKLOADS))
@@ -278,7 +278,8 @@ def main():
     # random-access rates of this GPU (the random-sector roofline's denominators)
     rates = binding.random_access_rates(gib=16, n_access=1 << 28)
     model = workload_model(args.workload)
-    mode = binding.REACH_PERSISTENT if args.mode == "persistent" else binding.REACH_PER_LEVEL
+    mode = {"persistent": binding.REACH_PERSISTENT, "per-level": binding.REACH_PER_LEVEL,
+            "graph": binding.REACH_GRAPH}[args.mode]
     ctx = binding.ReachContext(LOG2_BUCKETS, model.state_words, max_levels=MAX_LEVELS,
                                line_buckets=args.line_buckets)
     ctx.load(model)
@@ -356,7 +357,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": (NCU_TRAFFIC_BYTES.get(args.workload) if mode == 0 else None),
-                     "kernel": "k_reach_persistent" if mode == 0 else "k_reach_level",
+                     "kernel": {0: "k_reach_persistent", 1: "k_reach_level", 2: "k_reach_step"}[mode],
                      "kernel_ms": kernel_ms, "algorithmic_bytes": alg, "peak_source": which},
         "random_roofline": random_roofline(got.states, got.transitions, kernel_ms, rates, peak,
                                            model.state_words),

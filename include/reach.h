@@ -255,6 +255,8 @@ typedef struct {
 enum {
   REACH_PERSISTENT = 0, /* one cooperative launch runs every level (device-side level barrier) */
   REACH_PER_LEVEL = 1,  /* one launch per level; the host reads each level's size */
+  REACH_GRAPH = 2,      /* CUDA graphs of 32 level launches each (captured once per loaded
+                           model); the host looks at the search only between graphs */
   REACH_TRACE = 4       /* flag, with REACH_PERSISTENT and the default line length: record
                            predecessors so that reach_ctx_deadlock_trace can print a trace */
 };
@@ -291,7 +293,8 @@ ht_status reach_ctx_load(reach_ctx_t* c, const reach_model* m, const int32_t* in
 
 /* Clear the table and explore from the loaded init.  REACH_PERSISTENT enqueues
  * everything and returns without waiting; REACH_PER_LEVEL waits on the stream
- * once per level.  Results stay on the device until reach_ctx_result. */
+ * once per level; REACH_GRAPH waits once per 32 levels.  Results stay on the
+ * device until reach_ctx_result. */
 ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream);
 
 /* Wait for the stream and copy the result (and up to max_levels level sizes,

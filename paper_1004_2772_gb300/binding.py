@@ -22,7 +22,7 @@ from . import _build
 
 (HT_OK, HT_ERR_INVALID, HT_ERR_OOM, HT_ERR_FULL, HT_ERR_TIMEOUT, HT_ERR_CUDA, HT_ERR_LEVELS,
  HT_ERR_TOO_BIG) = range(8)
-REACH_PERSISTENT, REACH_PER_LEVEL, REACH_TRACE = 0, 1, 4
+REACH_PERSISTENT, REACH_PER_LEVEL, REACH_GRAPH, REACH_TRACE = 0, 1, 2, 4
 STATUS_NAMES = {0: "HT_OK", 1: "HT_ERR_INVALID", 2: "HT_ERR_OOM", 3: "HT_ERR_FULL",
                 4: "HT_ERR_TIMEOUT", 5: "HT_ERR_CUDA", 6: "HT_ERR_LEVELS", 7: "HT_ERR_TOO_BIG"}
 

@@ -42,6 +42,7 @@ static uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 using namespace vss;
 
 constexpr int kTimingRing = 64;  // kernel timings kept per context
+constexpr uint32_t kGraphLevels = 32;  // levels per graph of the graph driver
 
 struct reach_ctx {
   ht_t table;
@@ -69,6 +70,11 @@ struct reach_ctx {
   int coop = 0;
   // start / end events of the expansion kernels of the last kTimingRing runs
   cudaEvent_t ev[kTimingRing][2] = {};
+  // graph driver: instantiated graphs of kGraphLevels levels each, chunk c
+  // covering levels [c * kGraphLevels, (c + 1) * kGraphLevels); rebuilt after
+  // every load (the kernels' arguments follow the loaded model)
+  std::vector<cudaGraphExec_t> graphs;
+  cudaStream_t capture_stream = nullptr;
   uint64_t runs = 0;  // runs started; run r uses slot r % kTimingRing
   uint32_t last_launches = 0;
 };
@@ -184,6 +190,78 @@ static ReachDev make_rd(reach_ctx_t* c) {
 static size_t smem_bytes_for(reach_ctx_t* c, int threads) {
   return (size_t)((c->smem_words + 3) & ~3) * 4 +
          (size_t)(threads / 32) * warp_smem_words_nv((int)c->table.view.nv) * 4;
+}
+
+// Graph driver: capture chunk `chunk` (kGraphLevels levels, the seed first in
+// chunk 0) once, then replay it.
+static ht_status chunk_graph(reach_ctx_t* c, uint32_t chunk, const ReachKernels& ks, TableView tv,
+                             ReachDev rd, int threads, size_t smem, cudaGraphExec_t* out) {
+  if (chunk < c->graphs.size() && c->graphs[chunk]) {
+    *out = c->graphs[chunk];
+    return HT_OK;
+  }
+  if (!c->capture_stream)
+    VSS_CUDA_TRY(cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+  int per_sm = 0;
+  VSS_CUDA_TRY(cudaFuncSetAttribute(ks.step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.step, threads, smem));
+  if (per_sm < 1) return HT_ERR_INVALID;
+  const int blocks = per_sm * c->table.num_sms;
+  cudaStream_t cs = c->capture_stream;
+  cudaGraph_t graph = nullptr;
+  VSS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  if (chunk == 0) ks.seed<<<1, 1, 0, cs>>>(tv, rd);
+  for (uint32_t i = 0; i < kGraphLevels; ++i) {
+    const uint32_t k = chunk * kGraphLevels + i;
+    cudaMemsetAsync(&c->tot->counts[(k + 1) % 3], 0, 4, cs);
+    cudaMemsetAsync(&c->tot->cursor[k % 3], 0, 4, cs);
+    ks.step<<<blocks, threads, smem, cs>>>(tv, rd, k);
+  }
+  const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+  if (e != cudaSuccess || !graph) {
+    cudaGetLastError();
+    return HT_ERR_CUDA;
+  }
+  cudaGraphExec_t exec = nullptr;
+  const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    return HT_ERR_CUDA;
+  }
+  if (c->graphs.size() <= chunk) c->graphs.resize(chunk + 1, nullptr);
+  c->graphs[chunk] = exec;
+  *out = exec;
+  return HT_OK;
+}
+
+static ht_status run_graphs(reach_ctx_t* c, const ReachKernels& ks, TableView tv, ReachDev rd,
+                            int threads, size_t smem, cudaStream_t s) {
+  cudaEvent_t* ev = c->ev[c->runs % kTimingRing];
+  c->runs++;
+  VSS_CUDA_TRY(cudaEventRecord(ev[0], s));
+  c->last_launches = 0;
+  for (uint32_t chunk = 0;; ++chunk) {
+    cudaGraphExec_t g = nullptr;
+    ht_status st = chunk_graph(c, chunk, ks, tv, rd, threads, smem, &g);
+    if (st != HT_OK) return st;
+    VSS_CUDA_TRY(cudaGraphLaunch(g, s));
+    VSS_CUDA_TRY(cudaEventRecord(ev[1], s));
+    c->last_launches += kGraphLevels + (chunk == 0 ? 1 : 0);
+    // the next chunk only if the search is still going at its first level
+    const uint32_t k_next = (chunk + 1) * kGraphLevels;
+    VSS_CUDA_TRY(cudaMemcpyAsync(c->host_tot, c->tot, sizeof(ReachTotals), cudaMemcpyDeviceToHost, s));
+    VSS_CUDA_TRY(cudaMemcpyAsync(&c->host_tot->pad, &c->table.view.ctr->err, 4,
+                                 cudaMemcpyDeviceToHost, s));
+    VSS_CUDA_TRY(cudaStreamSynchronize(s));
+    if (c->host_tot->pad) break;  // latched error: the result reports it
+    if (c->host_tot->counts[k_next % 3] == 0) break;
+    if (k_next >= c->max_levels) {  // the search goes on past the level capacity
+      c->host_status = HT_ERR_LEVELS;
+      break;
+    }
+  }
+  return HT_OK;
 }
 
 extern "C" {
@@ -316,8 +394,16 @@ ht_status reach_ctx_create(int log2_buckets, int max_state_words, uint32_t max_l
   return HT_OK;
 }
 
+static void drop_graphs(reach_ctx_t* c) {
+  for (cudaGraphExec_t g : c->graphs)
+    if (g) cudaGraphExecDestroy(g);
+  c->graphs.clear();
+}
+
 ht_status reach_ctx_destroy(reach_ctx_t* c) {
   if (!c) return HT_ERR_INVALID;
+  drop_graphs(c);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   if (c->host_tot) cudaFreeHost(c->host_tot);
   for (int i = 0; i < kTimingRing; ++i)
     for (int j = 0; j < 2; ++j)
@@ -407,6 +493,7 @@ ht_status reach_ctx_load(reach_ctx_t* c, const reach_model* m, const int32_t* in
   if (st != HT_OK) return st;
   c->smem_words = c->host_blob[11];
   if (smem_bytes_for(c, (int)c->table.params.block_threads) > 200 * 1024) return HT_ERR_INVALID;
+  drop_graphs(c);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // synchronous w.r.t. the host buffer: the blob vector may change on the next load
   VSS_CUDA_TRY(cudaMemcpyAsync(c->blob, c->host_blob.data(), c->host_blob.size() * 4,
@@ -420,7 +507,7 @@ ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
   if (!c || !c->loaded) return HT_ERR_INVALID;
   const bool trace = (mode & REACH_TRACE) != 0;
   mode &= ~REACH_TRACE;
-  if (mode != REACH_PERSISTENT && mode != REACH_PER_LEVEL) return HT_ERR_INVALID;
+  if (mode != REACH_PERSISTENT && mode != REACH_PER_LEVEL && mode != REACH_GRAPH) return HT_ERR_INVALID;
   if (trace && mode != REACH_PERSISTENT) return HT_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ht_status st = table_clear(&c->table, s);
@@ -456,6 +543,7 @@ ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
     c->last_launches = 1;
     return HT_OK;
   }
+  if (mode == REACH_GRAPH) return run_graphs(c, ks, tv, rd, threads, smem, s);
   // per-level: one launch per level, the host reads each level's size
   VSS_CUDA_TRY(cudaFuncSetAttribute(ks.level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;

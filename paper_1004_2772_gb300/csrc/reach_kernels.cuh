@@ -285,6 +285,36 @@ __global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_level(TableView t
   flush_acc(t, rd, acc, lc);
 }
 
+// One level of the graph driver: a CUDA graph holds a fixed run of these, one
+// per level, each preceded by zeroing the next level's count and this
+// level's cursor.  A level whose frontier is empty (the search ended before
+// it) or that comes after an error returns at once; an active level records
+// its size before expanding.
+template <int NV, int L, int BW>
+__global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_step(TableView t, ReachDev rd, uint32_t k) {
+  const uint32_t n_cur = ld_relaxed(&rd.tot->counts[k % 3]);
+  if (n_cur == 0 || ld_relaxed(&t.ctr->err) != 0) return;
+  if (k >= rd.max_levels) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) latch_error(t.ctr, HT_ERR_LEVELS);
+    return;
+  }
+  if (k > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    rd.level_sizes[k] = n_cur;
+    rd.tot->n_levels = k + 1;
+  }
+  extern __shared__ int smem[];
+  const SModel m = load_model_smem(rd, smem);
+  uint32_t* wsm = reinterpret_cast<uint32_t*>(smem + ((rd.smem_words + 3) & ~3)) +
+                  (threadIdx.x >> 5) * warp_smem_words_nv(NV);
+  Acc acc;
+  LocalCounters lc;
+  const uint4* cur = (k & 1) ? rd.frontier1 : rd.frontier0;
+  uint4* next = (k & 1) ? rd.frontier0 : rd.frontier1;
+  run_level<NV, L, BW>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next,
+                       &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc, wsm);
+  flush_acc(t, rd, acc, lc);
+}
+
 // ---------------------------------------------------------------------------
 // Dispatch tables: each reach_k*.cu instantiates a share of the shapes.
 // ---------------------------------------------------------------------------
@@ -293,6 +323,7 @@ struct ReachKernels {
   void (*persistent_trace)(TableView, ReachDev);  // nullptr: shape compiled without tracing
   void (*seed)(TableView, ReachDev);
   void (*level)(TableView, ReachDev, uint32_t);
+  void (*step)(TableView, ReachDev, uint32_t);  // graph driver's level
 };
 
 template <int NV, int L, int BW>
@@ -302,7 +333,7 @@ static ReachKernels kernels_for() {
   constexpr bool kTrace = (BW == 32 ? L == 32 : L == 16);
   return {k_reach_persistent<NV, L, BW, false>,
           kTrace ? k_reach_persistent<NV, L, BW, kTrace> : nullptr, k_reach_seed<NV, L, BW>,
-          k_reach_level<NV, L, BW>};
+          k_reach_level<NV, L, BW>, k_reach_step<NV, L, BW>};
 }
 
 template <int NV>

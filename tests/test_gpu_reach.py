@@ -14,7 +14,7 @@ from test_oracle_pins import TINY_BEEM
 
 pytestmark = pytest.mark.gpu
 
-MODES = [0, 1]  # REACH_PERSISTENT, REACH_PER_LEVEL
+MODES = [0, 1, 2]  # REACH_PERSISTENT, REACH_PER_LEVEL, REACH_GRAPH
 
 
 def log2_for(states, lf=0.5):

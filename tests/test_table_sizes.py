@@ -163,7 +163,7 @@ def test_fused_stream_non_pow2(cuda_lib):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_reach_non_pow2(cuda_lib, mode):
     from test_gpu_reach import check
     m = synth.tiny_interleaving_model()
@@ -181,7 +181,7 @@ def test_beem_shaped_medium_non_pow2(cuda_lib):
     m = synth.beem_shaped_model(**g["model"])
     nb = _prime_lines_near(int(1.5 * g["states"]) // 32) * 32        # load factor ~0.67
     ctx = cuda_lib.ReachContext(None, 16, max_levels=4096, n_buckets=nb)
-    for mode in (0, 1):
+    for mode in (0, 1, 2):
         got = ctx.reach(m, mode=mode)
         assert (got.states, got.transitions, got.deadlocks, got.digest) == (
             g["states"], g["transitions"], g["deadlocks"], int(g["digest"], 16))
