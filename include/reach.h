@@ -350,9 +350,12 @@ ht_status reach(reach_ctx_t* c, const reach_model* m, const int32_t* init_host, 
  * buckets (NULL or 0: an estimate -- twice the product of the local state
  * counts when the model has no shared variables, capped at 2^16) and grow at
  * a level boundary when the coming level could push them past 90% load: a new
- * table from a device pool, sized for 50% load (never beyond the estimate's
- * bound), the old one re-inserted.  Unlike the paper's fixed table (Section
- * 3.1), this lets one launch serve models whose sizes are only estimated.
+ * table from a device pool, the old one re-inserted.  A model with a state
+ * bound (the product above) grows once, to a table that holds the bound at
+ * 50% load, when that table fits the pool; otherwise (no bound, or no room)
+ * the new table holds the coming level's estimate at 50% load.  Unlike the
+ * paper's fixed table (Section 3.1), this lets one launch serve models whose
+ * sizes are only estimated.
  * Results are bit-identical to reach() on each model alone.
  *
  * pool_bytes must cover every model's initial table generation plus all

@@ -285,8 +285,22 @@ __device__ void advance(BatchModel& M, const BatchGlobal& g, uint32_t e, uint32_
   const unsigned long long bound = M.states_bound;
   if (bound) need = fmin(need, (double)bound);
   if (need > g.grow_at * cap) {
-    uint32_t nl = lg + 1;
-    while (nl < 31 && (double)(1ull << nl) * g.grow_to < need) ++nl;
+    auto size_for = [&](double states) {
+      uint32_t s = lg + 1;
+      while (s < 31 && (double)(1ull << s) * g.grow_to < states) ++s;
+      return s;
+    };
+    // a model that outgrows its first table and has a state bound grows once,
+    // straight to the bound's size (if that fits the pool): its table then
+    // ends at load grow_to instead of up to grow_at, and the states are
+    // re-inserted once instead of at every doubling
+    uint32_t nl = size_for(need);
+    if (bound) {
+      const uint32_t nlb = size_for((double)bound);
+      if (nlb > nl && (1ull << nlb) / kClearUnit <= kUnitsMax &&
+          ld_relaxed64(&g.st->pool_used) + generation_bytes(nlb, M.nv) <= g.pool_bytes)
+        nl = nlb;
+    }
     if ((1ull << nl) / kClearUnit <= kUnitsMax) {
       const uint64_t bytes = generation_bytes(nl, M.nv);
       const unsigned long long off = atomicAdd(&g.st->pool_used, (unsigned long long)bytes);
