@@ -411,6 +411,7 @@ def random_access_rates(gib: float = 16, n_access: int = 1 << 28, device="cuda",
         ms = min(vss_probe_random(ptr, nbytes, n_access, mode, current_stream()) for _ in range(3))
         out[mode] = n_access / (ms / 1e3)
     del buf
+    torch.cuda.empty_cache()  # hand the probe buffer back to the driver
     return out
 
 

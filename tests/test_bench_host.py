@@ -61,6 +61,16 @@ def test_random_roofline_arithmetic():
     assert abs(r["frac"] - want_s * 1e3) < 1e-12
 
 
+def test_random_bound_scales_with_row_width():
+    rates = {0: 1e9, 1: 5e8, 2: 1e9, 3: 1e9}
+    # 32-byte rows (W <= 8): the compare is one 32 B read, a new state two sector writes
+    got = bench.random_bound_s(states=11, transitions=20, rates=rates, hbm_gbs=1.0, state_words=8)
+    assert abs(got - (20 / 1e9 + 10 / 1e9 + 2 * 10 / 1e9 + 2 * 11 * 32 / 1e9)) < 1e-15
+    # 128-byte rows (W = 32): two 64 B reads per compare, five sector writes per new state
+    got = bench.random_bound_s(states=11, transitions=20, rates=rates, hbm_gbs=1.0, state_words=32)
+    assert abs(got - (20 / 1e9 + 10 * 2 / 5e8 + 5 * 10 / 1e9 + 2 * 11 * 128 / 1e9)) < 1e-15
+
+
 def test_clock_summary_parses_nvidia_smi_lines():
     c = bench.ClockSampler(0)
     c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Active",
