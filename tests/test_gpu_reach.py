@@ -221,3 +221,45 @@ def test_run_times_ring(cuda_lib):
     assert t.shape[0] == 64 and (t > 0).all()
     assert abs(float(t[-1]) - ctx.last_timing()[0]) < 1e-6
     assert ctx.result().states == 100000
+
+
+def _stored_rows(b, ctx, W):
+    """The state vectors held by the done buckets of a context's table."""
+    import torch
+    bk, d, rw = b.ht_arrays(ctx.table_handle())
+    base = ctx.mem.data_ptr()
+    nb = ctx.n_buckets
+    torch.cuda.synchronize()
+    words = ctx.mem[bk - base:bk - base + 4 * nb].view(torch.int32).cpu().numpy()
+    rows = ctx.mem[d - base:d - base + 4 * nb * rw].view(torch.int32).view(nb, rw).cpu().numpy()
+    done = (words.view(np.uint32) >> 31) == 1
+    return rows[done][:, :W]
+
+
+def _sorted_rows(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a[np.lexsort(a.T[::-1])]
+
+
+@pytest.mark.parametrize("which", ["tiny", "guarded", "batched", "medium"])
+def test_stored_set_is_exactly_the_reachable_set(cuda_lib, which):
+    """The invariants beyond the counts: the done buckets hold pairwise
+    distinct vectors, and these are exactly the states the oracle's BFS
+    enumerates (nothing unreachable stored, nothing reachable missing)."""
+    if which == "tiny":
+        m = synth.tiny_interleaving_model()
+    elif which == "guarded":
+        m = synth.beem_shaped_model(3, n_procs=9, update_pct=40)        # 3,011 states, 80 deadlocks
+    elif which == "batched":
+        m = synth.batched_models(count=1, first_seed=17, lo=1e3, hi=2e5)[0]
+    else:
+        m = synth.beem_shaped_model(**load_golden("beem_medium.json")["model"])  # 5.5M states
+    ref = oracle.reach(m, keep_states=True, keep_cap=1 << 23)
+    assert not ref.truncated and ref.state_list.shape[0] == ref.states
+    ctx = cuda_lib.ReachContext(log2_for(ref.states), m.state_words, max_levels=4096)
+    for mode in MODES:
+        check(cuda_lib, ctx, m, mode, ref)
+        got = _sorted_rows(_stored_rows(cuda_lib, ctx, m.state_words))
+        assert got.shape == (ref.states, m.state_words)
+        assert not (got[1:] == got[:-1]).all(axis=1).any()          # no vector stored twice
+        assert np.array_equal(got, _sorted_rows(ref.state_list))   # the reachable set itself
