@@ -225,7 +225,11 @@ ht_status ht_find_or_put_stream(ht_t* h, uint64_t seed, uint64_t n_ids, uint64_t
  *   not (crit[p] >= 0 and edge_dst[e] == crit[p] and another process q has
  *        crit[q] >= 0 and v[q] == crit[q]);
  * firing it sets v[p] = edge_dst[e] and, when upd_var[e] >= 0,
- * v[P + upd_var[e]] = upd_val[e].  Every enabled edge is one transition. */
+ * v[P + upd_var[e]] = upd_val[e].  Every enabled edge is one transition.
+ * Limits (HT_ERR_INVALID otherwise): the sum over processes of the largest
+ * out-degree of a local state is at most 960 (the successors of one state
+ * must fit one warp's round), and the packed model (about P + sum(n_local)
+ * + 5E words) fits 128 KiB. */
 typedef struct {
   int32_t n_procs;           /* P, >= 1 */
   int32_t n_shared;          /* S, >= 0 */

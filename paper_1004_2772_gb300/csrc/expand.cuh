@@ -7,7 +7,7 @@
 namespace vss {
 
 #ifndef VSS_DESC_CAP
-#define VSS_DESC_CAP 1024
+#define VSS_DESC_CAP 960  // with 16-word rows, four blocks of 8 warps fit in shared memory
 #endif
 constexpr int kDescCap = VSS_DESC_CAP;  // successor descriptors per warp and round
 

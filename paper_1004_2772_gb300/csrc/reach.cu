@@ -187,6 +187,19 @@ static ReachDev make_rd(reach_ctx_t* c) {
   return rd;
 }
 
+// Blocks per SM for a single-model launch.  On tables of at most 2^20
+// buckets the levels are short and latency-bound: the level barrier, whose
+// cost grows with the number of blocks, weighs more than the memory-level
+// parallelism of a fourth block per SM.
+#ifndef VSS_SMALL_TABLE_BLOCKS
+#define VSS_SMALL_TABLE_BLOCKS 3
+#endif
+static int blocks_per_sm(int occupancy, uint64_t nb) {
+  if (VSS_SMALL_TABLE_BLOCKS > 0 && nb <= (1ull << 20) && occupancy > VSS_SMALL_TABLE_BLOCKS)
+    return VSS_SMALL_TABLE_BLOCKS;
+  return occupancy;
+}
+
 static size_t smem_bytes_for(reach_ctx_t* c, int threads) {
   return (size_t)((c->smem_words + 3) & ~3) * 4 +
          (size_t)(threads / 32) * warp_smem_words_nv((int)c->table.view.nv) * 4;
@@ -206,7 +219,7 @@ static ht_status chunk_graph(reach_ctx_t* c, uint32_t chunk, const ReachKernels&
   VSS_CUDA_TRY(cudaFuncSetAttribute(ks.step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ks.step, threads, smem));
   if (per_sm < 1) return HT_ERR_INVALID;
-  const int blocks = per_sm * c->table.num_sms;
+  const int blocks = blocks_per_sm(per_sm, c->nb) * c->table.num_sms;
   cudaStream_t cs = c->capture_stream;
   cudaGraph_t graph = nullptr;
   VSS_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
@@ -532,7 +545,7 @@ ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
     int per_sm = 0;
     VSS_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
     if (per_sm < 1) return HT_ERR_INVALID;
-    const int blocks = per_sm * c->table.num_sms;
+    const int blocks = blocks_per_sm(per_sm, c->nb) * c->table.num_sms;
     void* args[] = {&tv, &rd};
     cudaEvent_t* ev = c->ev[c->runs % kTimingRing];
     VSS_CUDA_TRY(cudaEventRecord(ev[0], s));
@@ -560,7 +573,7 @@ ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
   for (uint32_t k = 0;; ++k) {
     const uint64_t warps_needed = (n_cur + 31) / 32;
     const uint64_t want = (warps_needed * 32 + threads - 1) / threads;
-    const uint64_t cap = (uint64_t)per_sm * c->table.num_sms;
+    const uint64_t cap = (uint64_t)blocks_per_sm(per_sm, c->nb) * c->table.num_sms;
     const int blocks = (int)std::max<uint64_t>(1, std::min(want, cap));
     VSS_CUDA_TRY(cudaMemsetAsync(&c->tot->counts[(k + 1) % 3], 0, 4, s));
     VSS_CUDA_TRY(cudaMemsetAsync(&c->tot->cursor[k % 3], 0, 4, s));
@@ -756,7 +769,8 @@ extern "C" ht_status reach_noalloc(const reach_model* m, const int32_t* init_hos
   rd.bar_spin = 1u << 22;
   void* args[] = {&tv, &rd};
   VSS_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(ks.persistent),
-                                           per_sm * table.num_sms, threads, args, smem, s));
+                                           blocks_per_sm(per_sm, nb) * table.num_sms, threads, args,
+                                           smem, s));
 
   ReachTotals t;
   DevCounters ctr;
@@ -823,8 +837,8 @@ ht_status solo_launch(const SoloRun& r, int line_buckets, int threads, cudaStrea
   rd.max_levels = r.max_levels;
   rd.bar_spin = 1u << 22;
   void* args[] = {&tv, &rd};
-  VSS_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(ks.persistent), per_sm * sms,
-                                           threads, args, smem, s));
+  VSS_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<void*>(ks.persistent),
+                                           blocks_per_sm(per_sm, nb) * sms, threads, args, smem, s));
   return HT_OK;
 }
 

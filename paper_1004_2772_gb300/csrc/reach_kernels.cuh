@@ -15,9 +15,19 @@ namespace vss {
 #ifndef VSS_BARRIER_STATS
 #define VSS_BARRIER_STATS 0  // measurement builds only: record barrier arrival spreads
 #endif
-#ifndef VSS_REACH_MINB
-#define VSS_REACH_MINB 3  // __launch_bounds__ minimum resident blocks of the expansion kernels
-#endif             // successor descriptors per warp and round
+// Resident blocks of 256 threads per SM that the expansion kernels are
+// compiled for (__launch_bounds__): four (64 registers) for rows of up to 16
+// words, where the shared memory of four blocks fits and the extra warps keep
+// more random accesses in flight; three (80 registers) for wider rows, whose
+// shared memory allows only three blocks anyway.
+template <int NV>
+constexpr int reach_min_blocks() {
+#ifdef VSS_REACH_MINB
+  return VSS_REACH_MINB;  // a fixed count for every width (measurement builds)
+#else
+  return NV <= 4 ? 4 : 3;
+#endif
+}
 constexpr int kModelMaxWords = 1 << 15;    // model blob capacity (int32 words, 128 KiB)
 constexpr int kHdr = 16;                   // blob header words
 
@@ -206,7 +216,7 @@ static __device__ bool grid_barrier(const ReachDev& rd, DevCounters* ctr, uint32
 }
 
 template <int NV, int L, int BW, bool TR>
-__global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_persistent(TableView t, ReachDev rd) {
+__global__ void __launch_bounds__(256, reach_min_blocks<NV>()) k_reach_persistent(TableView t, ReachDev rd) {
   extern __shared__ int smem[];
   const SModel m = load_model_smem(rd, smem);
   uint32_t* wsm = reinterpret_cast<uint32_t*>(smem + ((rd.smem_words + 3) & ~3)) +
@@ -270,7 +280,7 @@ __global__ void k_reach_seed(TableView t, ReachDev rd) {
 }
 
 template <int NV, int L, int BW>
-__global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_level(TableView t, ReachDev rd, uint32_t k) {
+__global__ void __launch_bounds__(256, reach_min_blocks<NV>()) k_reach_level(TableView t, ReachDev rd, uint32_t k) {
   extern __shared__ int smem[];
   const SModel m = load_model_smem(rd, smem);
   uint32_t* wsm = reinterpret_cast<uint32_t*>(smem + ((rd.smem_words + 3) & ~3)) +
@@ -291,7 +301,7 @@ __global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_level(TableView t
 // it) or that comes after an error returns at once; an active level records
 // its size before expanding.
 template <int NV, int L, int BW>
-__global__ void __launch_bounds__(256, VSS_REACH_MINB) k_reach_step(TableView t, ReachDev rd, uint32_t k) {
+__global__ void __launch_bounds__(256, reach_min_blocks<NV>()) k_reach_step(TableView t, ReachDev rd, uint32_t k) {
   const uint32_t n_cur = ld_relaxed(&rd.tot->counts[k % 3]);
   if (n_cur == 0 || ld_relaxed(&t.ctr->err) != 0) return;
   if (k >= rd.max_levels) {
