@@ -14,7 +14,7 @@ namespace vss {
 // shuffles and take its answer as "seen" -- this removes write-busy waits on
 // hot keys that arrive together.
 template <int NV, int L, bool DEDUP, int BW>
-__global__ void __launch_bounds__(256) k_find_or_put(TableView t, const int32_t* __restrict__ keys,
+__global__ void __launch_bounds__(256, table_min_blocks<NV>()) k_find_or_put(TableView t, const int32_t* __restrict__ keys,
                                                      uint64_t n, uint8_t* __restrict__ seen,
                                                      uint32_t* __restrict__ idx) {
   LocalCounters lc;

@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) k_gen_keys(StreamSpec s, uint64_t c0, uin
 // Fused generator + find-or-put.  Counts new keys and sums the fingerprints
 // of the keys it stored (the set digest of the fill).
 template <int NV, int L, bool DEDUP, int BW>
-__global__ void __launch_bounds__(256) k_find_or_put_stream(TableView t, StreamSpec s, uint64_t c0,
+__global__ void __launch_bounds__(256, table_min_blocks<NV>()) k_find_or_put_stream(TableView t, StreamSpec s, uint64_t c0,
                                                             uint64_t n, unsigned long long* out) {
   LocalCounters lc;
   unsigned long long n_new = 0, dig = 0;

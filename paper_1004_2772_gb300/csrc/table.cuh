@@ -36,6 +36,20 @@ namespace vss {
 //                every later load of the thread is ordered after them;
 //   0:           bucket sectors are read relaxed and an acquire fence is
 //                issued before a data row is compared.
+// Resident blocks of 256 threads per SM that the one-thread-per-key table
+// kernels are compiled for (__launch_bounds__): five (48 registers; with
+// 16-word rows about 120 bytes spill to L1) for rows of up to 16 words -- the
+// extra threads keep more random accesses in flight, measured 2 % faster than
+// four -- and four for wider rows, which would spill far more.
+template <int NV>
+constexpr int table_min_blocks() {
+#ifdef VSS_TABLE_MINB
+  return VSS_TABLE_MINB;  // a fixed count for every width (measurement builds)
+#else
+  return NV <= 4 ? 5 : 4;
+#endif
+}
+
 #ifndef VSS_ACQ_MODE
 #define VSS_ACQ_MODE 1
 #endif
