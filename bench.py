@@ -50,10 +50,10 @@ LOG2_BUCKETS = 26
 MAX_LEVELS = 1 << 14
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the workload's
 # kernel (ncu, 1 pass): k_reach_persistent on the full BEEM-shaped workload
-# (profiles/k_reach_persistent_beem-shaped.md) and k_reach_batch on 256 and 32
+# (profiles/k_reach_persistent_beem-shaped.md) and k_reach_batch on the 256
 # batched models (profiles/k_reach_batch_batched-256.md).  Must be re-measured
 # (or set to None) whenever the kernel changes.
-NCU_TRAFFIC_BYTES = {"beem": 24.47e9, "batch256": 75.76e9, "batch32": 5.52e9}
+NCU_TRAFFIC_BYTES = {"beem": 24.47e9, "batch256": 75.71e9}
 
 
 def workload_model(name="beem"):
