@@ -11,14 +11,6 @@ namespace vss {
 #endif
 constexpr int kDescCap = VSS_DESC_CAP;  // successor descriptors per warp and round
 
-#ifndef VSS_P_UNROLL
-// unrolling of the per-process loops of successor generation (0: the
-// compiler's choice); 4 lets the shared-memory loads of four processes'
-// tables overlap (C2 0.4 %, the medium model 1.2 % faster than 0)
-#define VSS_P_UNROLL 4
-#endif
-constexpr int kPUnroll = VSS_P_UNROLL > 0 ? VSS_P_UNROLL : 1;
-
 #ifndef VSS_WARP_DEDUP
 #define VSS_WARP_DEDUP 0  // merge equal successors of one warp iteration before probing
 #endif
@@ -114,18 +106,12 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
     const int* rw = reinterpret_cast<const int*>(rows + lane * RS);
     int ncrit = 0;
     if (m.crit_any) {
-#if VSS_P_UNROLL > 0
-#pragma unroll kPUnroll
-#endif
       for (int p = 0; p < P; ++p) {
         const int cp = m.crit[p];
         ncrit += (cp >= 0 && rw[p] == cp) ? 1 : 0;
       }
     }
     uint32_t* d = desc + lane * maxfan;
-#if VSS_P_UNROLL > 0
-#pragma unroll kPUnroll
-#endif
     for (int p = 0; p < P; ++p) {
       const int s = rw[p];
       const int b = m.base[p] + s;
