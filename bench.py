@@ -50,10 +50,12 @@ LOG2_BUCKETS = 26
 MAX_LEVELS = 1 << 14
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the workload's
 # kernel (ncu, 1 pass): k_reach_persistent on the full BEEM-shaped workload
-# (profiles/k_reach_persistent_beem-shaped.md) and k_reach_batch on the 256
-# batched models (profiles/k_reach_batch_batched-256.md).  Must be re-measured
+# (profiles/k_reach_persistent_beem-shaped.md), k_reach_batch on the 256
+# batched models (profiles/k_reach_batch_batched-256.md) and
+# k_find_or_put_stream on one 2^26-bucket fill at load 0.75, uniform reuse,
+# default parameters (profiles/k_find_or_put_stream_hashtable-2p24.md).  Must be re-measured
 # (or set to None) whenever the kernel changes.
-NCU_TRAFFIC_BYTES = {"beem": 24.47e9, "batch256": 75.71e9}
+NCU_TRAFFIC_BYTES = {"beem": 24.47e9, "batch256": 75.71e9, "hashtable-26-0.75-uniform-fused": 22.33e9}
 
 
 def workload_model(name="beem"):
@@ -449,7 +451,9 @@ def run_hashtable(args, world, rank, local, dev):
                       "calls_per_step": calls, "distinct_keys": n_ids, "params": params,
                       "l2": f"inputs larger than L2 (table {tab_gb:.1f} GB)"})
     line["roofline"] = {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
-                        "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": None,
+                        "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak,
+                        "traffic": (None if tuned or args.line_buckets != 32 else NCU_TRAFFIC_BYTES.get(
+                            f"hashtable-{log2}-{lf}-{args.dist}-{args.key_mode}")),
                         "algorithmic_bytes": alg, "peak_source": which}
     line["random_roofline"] = {"bound_ms": bound_s * 1e3, "frac": bound_s * 1e3 / ms,
                                "probe_rates_per_s": {"read32": rates[0], "read64": rates[1],
