@@ -53,7 +53,7 @@ MAX_LEVELS = 1 << 14
 # (profiles/k_reach_persistent_beem-shaped.md), k_reach_batch on the 256
 # batched models (profiles/k_reach_batch_batched-256.md) and
 # k_find_or_put_stream on one 2^26-bucket fill at load 0.75, uniform reuse,
-# default parameters (profiles/k_find_or_put_stream_hashtable-2p24.md).  Must be re-measured
+# default parameters (profiles/k_find_or_put_stream_hashtable-fill.md).  Must be re-measured
 # (or set to None) whenever the kernel changes.
 NCU_TRAFFIC_BYTES = {"beem": 24.47e9, "batch256": 75.71e9, "hashtable-26-0.75-uniform-fused": 22.33e9}
 
