@@ -460,9 +460,10 @@ ht_status serve_close(serve_t* s);
  *     not exceed 32 MiB (e.g. 2^18 buckets for W <= 8, 2^17 for W <= 16);
  *     larger requests return HT_ERR_TOO_BIG and enqueue nothing.
  *   - Allocates nothing: no cudaMalloc/cudaFree, no pinned host buffers, no
- *     events.  The array's device address is looked up once per device
- *     (cudaGetSymbolAddress) by the first call made with that device current;
- *     make that first call before any stream capture.
+ *     events.  Every call looks up the array's device address on the device
+ *     current at the call (cudaGetSymbolAddress, which allocates nothing), so
+ *     the address stays right after cudaDeviceReset and on a driver-API
+ *     context of the caller's own.
  *   - Every call reuses the same array and clears what must start at zero.
  *     Calls that overlap on the GPU (other streams, other host threads) race
  *     on it: serialise them.

@@ -19,7 +19,6 @@
 // results and the reach_* C ABI); the kernels are in reach_kernels.cuh.
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <vector>
 
@@ -655,35 +654,27 @@ ht_status reach(reach_ctx_t* c, const reach_model* m, const int32_t* init_host, 
 // allowed).  The table, the two frontiers and the counters live in one
 // file-scope device array of kNoAllocScratchBytes, loaded with the library and
 // held by every GPU that loads it until the process exits.  Host code cannot
-// use the array's name as a device address; its address is obtained once per
-// device with cudaGetSymbolAddress, on the first call made with that device
-// current.
+// use the array's name as a device address: every call looks the address up
+// with cudaGetSymbolAddress for the device (and context) current at the call.
+// The lookup allocates nothing, and looking it up each time, rather than
+// caching it per device, keeps a call correct after cudaDeviceReset (which
+// reloads the module at a new address) and on a caller's own driver-API
+// context (which holds its own copy of the module).
 // ---------------------------------------------------------------------------
 namespace vss {
 
 constexpr uint64_t kNoAllocScratchBytes = 32ull << 20;
-constexpr int kNoAllocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
-
 static ht_status noalloc_scratch(void** out) {
-  int dev = 0;
-  VSS_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return HT_ERR_INVALID;
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || p == nullptr) {
-      cudaGetLastError();
-      return HT_ERR_CUDA;
-    }
-    g_noalloc_addr[dev] = p;
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return HT_ERR_CUDA;
   }
-  *out = g_noalloc_addr[dev];
+  *out = p;
   return HT_OK;
 }
 
