@@ -45,6 +45,7 @@ WORKLOADS = {
     "hashtable-sweep": (None, 0),
     "batch": (None, 0),
     "serve": (None, 0),
+    "probe-sweep": (None, 0),
 }
 LOG2_BUCKETS = 26
 MAX_LEVELS = 1 << 14
@@ -283,9 +284,9 @@ def main():
     dev = torch.device("cuda", local)
     _build.build()
     binding.load()
-    if args.workload in ("hashtable", "hashtable-sweep", "batch", "serve"):
+    if args.workload in ("hashtable", "hashtable-sweep", "batch", "serve", "probe-sweep"):
         {"hashtable": run_hashtable, "hashtable-sweep": run_hashtable_sweep, "batch": run_batch,
-         "serve": run_serve}[args.workload](args, world, rank, local, dev)
+         "serve": run_serve, "probe-sweep": run_probe_sweep}[args.workload](args, world, rank, local, dev)
         return
 
     # random-access rates of this GPU (the random-sector roofline's denominators)
@@ -693,6 +694,26 @@ def run_serve(args, world, rank, local, dev):
                                             "p99_ms": float(np.percentile(lat_plain, 99)),
                                             "note": "device time of each job alone via reach(), queued in arrival order; host overheads excluded"}
     line["gpu_launches"] = c["kernel_launches"]
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_probe_sweep(args, world, rank, local, dev):
+    """The random-access probe in every swept shape (accesses in flight per
+    thread x blocks per SM x threads per block) for every mode, over a 16 GiB
+    buffer: the plateau of each mode is the roofline denominator bench.py
+    uses.  value = the plateau of 32-byte sector reads."""
+    from paper_1004_2772_gb300 import binding
+    with ClockSampler(local) as clocks:
+        rows = binding.probe_sweep(gib=16, n_access=1 << 28, modes=tuple(range(9)))
+    best = {m: max((r for r in rows if r["mode"] == m), key=lambda r: r["per_s"]) for m in range(9)}
+    line = base_line(args, world, "random 32-byte sector reads/sec on 1 GB300 (probe plateau)",
+                     best[0]["per_s"], "accesses/s", None,
+                     {"workload": "random-access-probe-16GiB", "accesses_per_run": 1 << 28,
+                      "l2": "16 GiB buffer, larger than L2"})
+    line["plateau"] = {binding.PROBE_MODES[m]: best[m] for m in range(9)}
+    line["rows"] = rows
+    line["clocks"] = clocks.summary()
     if rank == 0:
         print(json.dumps(line), flush=True)
 

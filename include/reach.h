@@ -484,10 +484,27 @@ ht_status reach_noalloc(const reach_model* m, const int32_t* init_host, int log2
  *   4  32-bit compare-and-swap          5  16-bit compare-and-swap
  *   6  32-bit relaxed store             7  16-bit relaxed store
  * (4..7 are the claim and publish steps of an insert for either bucket width.)
- * Every thread keeps 8 accesses in flight.  *ms = device time from CUDA events
- * on `stream`.  Synchronous.  Use a buffer much larger than L2 (e.g. 16 GiB). */
+ * Every thread keeps 8 accesses in flight; 8 blocks of 256 threads per SM.
+ * Unit k of an access is a multiply-high range reduction of a SplitMix64 hash
+ * of the access number (no division).  *ms = device time from CUDA events on
+ * `stream`.  Synchronous.  Use a buffer much larger than L2 (e.g. 16 GiB). */
 ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_access, int mode, void* stream,
                            float* ms);
+
+/* The same probe in a shape chosen by the caller, for finding where the rate
+ * stops growing with the requests in flight: `inflight` accesses issued by
+ * each thread before it consumes any (1, 2, 4, 8, 16, 32 or 64; reads of 32
+ * bytes up to 16 and of 64 bytes up to 8, because they hold their data in
+ * registers), a grid of blocks_per_sm (1..64) blocks per SM of `threads`
+ * (32..256, a multiple of 32) threads; 0 in any of the three selects 8, 8
+ * and 256.  Blocks beyond those resident at once (a shape's registers set
+ * that number) run in waves.  One more mode:
+ *   8  read 4 bytes of a random 32-byte sector (DRAM still moves the sector
+ *      into L2; 4 bytes go back to the SM: the memory side of mode 0)
+ * HT_ERR_INVALID for a shape or mode outside these.  Synchronous. */
+ht_status vss_probe_random_cfg(void* buf_dev, uint64_t bytes, uint64_t n_access, int mode,
+                               int inflight, int blocks_per_sm, int threads, void* stream,
+                               float* ms);
 
 /* Human-readable name of a status code (static storage). */
 const char* ht_status_string(ht_status s);

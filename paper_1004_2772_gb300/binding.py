@@ -39,7 +39,7 @@ EXPORTED = [
     "serve_close", "reach_ctx_deadlock_trace",
     "ht_bytes_n", "ht_create_n_at", "ht_buckets_for_bytes", "vss_line_divide",
     "reach_ctx_bytes_n", "reach_ctx_create_n_at", "reach_ctx_buckets_for_bytes",
-    "reach_ctx_run_times",
+    "reach_ctx_run_times", "vss_probe_random_cfg",
 ]
 
 
@@ -125,6 +125,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "reach_ctx_last_timing": [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_uint32)],
         "reach_ctx_level_ns": [_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)],
         "vss_probe_random": [_VP, _u64, _u64, _i, _VP, ctypes.POINTER(ctypes.c_float)],
+        "vss_probe_random_cfg": [_VP, _u64, _u64, _i, _i, _i, _i, _VP, ctypes.POINTER(ctypes.c_float)],
         "vss_gen_keys": [_u64, _u64, _u64, _u64, _VP, _i, _VP, _VP],
         "ht_find_or_put_stream": [_VP, _u64, _u64, _u64, _u64, _VP, _VP, _VP],
         "reach_batch_bytes": [_VP, _VP, _i, ctypes.c_uint32, _u64, ctypes.POINTER(_u64)],
@@ -394,13 +395,59 @@ def vss_probe_random(buf_dev: int, nbytes: int, n_access: int, mode: int, stream
     return ms.value
 
 
+def vss_probe_random_cfg(buf_dev: int, nbytes: int, n_access: int, mode: int, inflight: int,
+                         blocks_per_sm: int, threads: int, stream: int = 0) -> float:
+    ms = ctypes.c_float()
+    _check(load().vss_probe_random_cfg(buf_dev, nbytes, n_access, mode, inflight, blocks_per_sm,
+                                       threads, stream, ctypes.byref(ms)), "vss_probe_random_cfg")
+    return ms.value
+
+
 PROBE_MODES = {0: "read 32 B", 1: "read 64 B", 2: "write 32 B", 3: "atomic 32-bit",
-               4: "CAS 32-bit", 5: "CAS 16-bit", 6: "store 32-bit", 7: "store 16-bit"}
+               4: "CAS 32-bit", 5: "CAS 16-bit", 6: "store 32-bit", 7: "store 16-bit",
+               8: "read 4 B of a 32 B sector"}
+
+# Probe shapes swept for each mode: (accesses in flight per thread, blocks per
+# SM, threads per block).  Reads hold their data in registers, so their
+# resident blocks per SM fall as the in-flight count grows; the shapes keep
+# several thousand requests in flight per SM in every case.
+PROBE_SHAPES = {
+    0: [(i, b, t) for i in (2, 4, 8, 16) for b in (8, 32) for t in (128, 256)],
+    1: [(i, b, t) for i in (2, 4, 8) for b in (8, 32) for t in (128, 256)],
+    8: [(i, b, t) for i in (4, 8, 16, 32, 64) for b in (8, 32) for t in (128, 256)],
+}
+DEFAULT_WRITE_SHAPES = [(i, b, 256) for i in (4, 8, 16) for b in (8, 32)]
+
+
+def probe_sweep(gib: float = 16, n_access: int = 1 << 28, device="cuda", modes=(0, 1, 2, 3),
+                reps: int = 3, shapes: dict | None = None) -> list:
+    """Random accesses per second of every (mode, shape) in the sweep: a list
+    of {"mode", "inflight", "blocks_per_sm", "threads", "per_s"} (best of reps)."""
+    torch = _torch()
+    nbytes = int(gib * (1 << 30)) // 256 * 256
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+    ptr = (buf.data_ptr() + 255) // 256 * 256
+    rows = []
+    for mode in modes:
+        for (inf, bps, thr) in (shapes or PROBE_SHAPES).get(mode, DEFAULT_WRITE_SHAPES):
+            vss_probe_random_cfg(ptr, nbytes, n_access // 8, mode, inf, bps, thr, current_stream())
+            ms = min(vss_probe_random_cfg(ptr, nbytes, n_access, mode, inf, bps, thr, current_stream())
+                     for _ in range(reps))
+            rows.append({"mode": mode, "inflight": inf, "blocks_per_sm": bps, "threads": thr,
+                         "per_s": n_access / (ms / 1e3)})
+    del buf
+    torch.cuda.empty_cache()  # hand the probe buffer back to the driver
+    return rows
 
 
 def random_access_rates(gib: float = 16, n_access: int = 1 << 28, device="cuda",
-                        modes=(0, 1, 2, 3)) -> dict:
-    """Random accesses per second for the given probe modes over a `gib` GiB buffer."""
+                        modes=(0, 1, 2, 3), sweep: bool = True) -> dict:
+    """Random accesses per second for each probe mode over a `gib` GiB buffer:
+    the best rate over the probe shapes of PROBE_SHAPES (the plateau) when
+    sweep is set, else the fixed default shape."""
+    if sweep:
+        rows = probe_sweep(gib, n_access, device, modes)
+        return {m: max(r["per_s"] for r in rows if r["mode"] == m) for m in modes}
     torch = _torch()
     nbytes = int(gib * (1 << 30)) // 256 * 256
     buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
@@ -411,7 +458,7 @@ def random_access_rates(gib: float = 16, n_access: int = 1 << 28, device="cuda",
         ms = min(vss_probe_random(ptr, nbytes, n_access, mode, current_stream()) for _ in range(3))
         out[mode] = n_access / (ms / 1e3)
     del buf
-    torch.cuda.empty_cache()  # hand the probe buffer back to the driver
+    torch.cuda.empty_cache()
     return out
 
 

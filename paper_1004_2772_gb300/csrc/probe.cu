@@ -3,15 +3,14 @@
 // The store's hot path moves data in 32-byte L2 sectors at random addresses
 // (one bucket sector per probe, one or two sectors per data row).  This
 // kernel measures how many such random accesses per second the GPU's memory
-// system sustains, with the same access shapes: every thread issues
-// kInflight independent accesses to sectors chosen by a counter-based hash
-// (SplitMix64 output function of the access number) before it consumes any,
-// so the number of requests in flight is limited only by residency.
+// system sustains, with the same access shapes: every thread issues INF
+// independent accesses to sectors chosen by a counter-based hash (SplitMix64
+// output function of the access number) before it consumes any.  The caller
+// picks INF, the blocks per SM and the threads per block, so a sweep over
+// them finds the rate's plateau rather than the limit of one probe shape.
 #include "internal.h"
 
 namespace vss {
-
-constexpr int kInflight = 8;
 
 __device__ __forceinline__ uint64_t probe_mix(uint64_t z) {
   z += 0x9E3779B97F4A7C15ULL;
@@ -20,36 +19,57 @@ __device__ __forceinline__ uint64_t probe_mix(uint64_t z) {
   return z ^ (z >> 31);
 }
 
+// Unit number of access a: a multiply-high range reduction of a counter-based
+// hash (uniform over [0, n_units) up to a bias below 2^-32 for n_units < 2^32;
+// no 64-bit division on the access path).
+__device__ __forceinline__ uint64_t probe_unit(uint64_t seed, uint64_t a, uint64_t n_units) {
+  return __umul64hi(probe_mix(seed ^ a), n_units);
+}
+
 // mode 0: read one 32 B sector; 1: read 64 B (two adjacent sectors, 64 B
 // aligned); 2: write one 32 B sector; 3: atomicAdd on one 32-bit word;
 // 4 / 5: compare-and-swap (0 -> x) on a 32- / 16-bit word; 6 / 7: relaxed
 // gpu-scope store of one 32- / 16-bit word (the claim and publish steps of an
-// insert, for either bucket width).
-template <int MODE>
-__global__ void __launch_bounds__(256) k_probe(uint4* buf, uint64_t n_units, uint64_t n_access,
-                                               uint64_t seed, unsigned long long* sink) {
+// insert, for either bucket width); 8: read 4 bytes of a random 32 B sector
+// (the whole sector still comes from DRAM into L2, only 4 bytes go back to
+// the SM: the memory side of mode 0 without its return traffic).
+// INF accesses per thread are issued before any is consumed.
+template <int MODE, int INF>
+__global__ void __launch_bounds__(256, 1) k_probe(uint4* buf, uint64_t n_units, uint64_t n_access,
+                                                uint64_t seed, unsigned long long* sink) {
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
   uint32_t acc = 0;
-  for (uint64_t base = tid * kInflight; base < n_access; base += nthr * kInflight) {
-    uint64_t u[kInflight];
+  uint64_t base = tid * INF;
+  for (; base < n_access; base += nthr * INF) {
+    uint64_t u[INF];
 #pragma unroll
-    for (int k = 0; k < kInflight; ++k) u[k] = probe_mix(seed ^ (base + k)) % n_units;
-    if (MODE == 0 || MODE == 1) {
-      uint4 v[kInflight][MODE == 1 ? 4 : 2];
+    for (int k = 0; k < INF; ++k) u[k] = probe_unit(seed, base + k, n_units);
+    if (MODE == 0 || MODE == 1 || MODE == 8) {
+      if (base + INF > n_access) break;  // a partial group: the tail loop below
+      // whole groups are unpredicated and every word read is used, so each
+      // read keeps its own registers until all INF are issued
+      if (MODE == 8) {
+        uint32_t v[INF];
 #pragma unroll
-      for (int k = 0; k < kInflight; ++k) {
-        const uint4* p = buf + u[k] * (MODE == 1 ? 4 : 2);
+        for (int k = 0; k < INF; ++k) v[k] = __ldcg(reinterpret_cast<const unsigned int*>(buf + u[k] * 2));
 #pragma unroll
-        for (int q = 0; q < (MODE == 1 ? 4 : 2); q += 2) ld_cg_v8(p + q, v[k][q], v[k][q + 1]);
+        for (int k = 0; k < INF; ++k) acc ^= v[k];
+      } else {
+        constexpr int C = MODE == 1 ? 4 : 2;  // 16-byte chunks per unit
+        uint4 v[INF][C];
+#pragma unroll
+        for (int k = 0; k < INF; ++k)
+#pragma unroll
+          for (int q = 0; q < C; q += 2) ld_cg_v8(buf + u[k] * C + q, v[k][q], v[k][q + 1]);
+#pragma unroll
+        for (int k = 0; k < INF; ++k)
+#pragma unroll
+          for (int q = 0; q < C; ++q) acc ^= v[k][q].x ^ v[k][q].y ^ v[k][q].z ^ v[k][q].w;
       }
-#pragma unroll
-      for (int k = 0; k < kInflight; ++k)
-#pragma unroll
-        for (int q = 0; q < (MODE == 1 ? 4 : 2); ++q) acc ^= v[k][q].x ^ v[k][q].w;
     } else if (MODE == 2) {
 #pragma unroll
-      for (int k = 0; k < kInflight; ++k) {
+      for (int k = 0; k < INF; ++k) {
         if (base + k < n_access) {
           const uint4 w = make_uint4((uint32_t)u[k], (uint32_t)k, 0u, 0u);
           st_v8(buf + u[k] * 2, w, w);
@@ -57,41 +77,107 @@ __global__ void __launch_bounds__(256) k_probe(uint4* buf, uint64_t n_units, uin
       }
     } else if (MODE == 3) {
 #pragma unroll
-      for (int k = 0; k < kInflight; ++k)
+      for (int k = 0; k < INF; ++k)
         if (base + k < n_access) atomicAdd(reinterpret_cast<uint32_t*>(buf + u[k] * 2), 1u);
     } else if (MODE == 4) {
 #pragma unroll
-      for (int k = 0; k < kInflight; ++k)
+      for (int k = 0; k < INF; ++k)
         if (base + k < n_access)
           acc ^= atomicCAS(reinterpret_cast<uint32_t*>(buf + u[k] * 2), 0u, (uint32_t)u[k] | 1u);
     } else if (MODE == 5) {
 #pragma unroll
-      for (int k = 0; k < kInflight; ++k)
+      for (int k = 0; k < INF; ++k)
         if (base + k < n_access)
           acc ^= atomicCAS(reinterpret_cast<unsigned short*>(buf + u[k] * 2), (unsigned short)0,
                            (unsigned short)(u[k] | 1u));
     } else if (MODE == 6) {
 #pragma unroll
-      for (int k = 0; k < kInflight; ++k)
+      for (int k = 0; k < INF; ++k)
         if (base + k < n_access) st_relaxed(reinterpret_cast<uint32_t*>(buf + u[k] * 2), (uint32_t)k);
     } else {
 #pragma unroll
-      for (int k = 0; k < kInflight; ++k)
+      for (int k = 0; k < INF; ++k)
         if (base + k < n_access)
           st_relaxed_u16(reinterpret_cast<uint16_t*>(buf + u[k] * 2), (uint32_t)k);
     }
   }
+  // reads of the last partial group (at most INF - 1 per thread), one at a time
+  if (MODE == 0 || MODE == 1 || MODE == 8) {
+    for (uint64_t a = base; a < n_access && a < base + INF; ++a) {
+      const uint64_t u = probe_unit(seed, a, n_units);
+      if (MODE == 8) {
+        acc ^= __ldcg(reinterpret_cast<const unsigned int*>(buf + u * 2));
+      } else {
+        constexpr int C = MODE == 1 ? 4 : 2;
+        for (int q = 0; q < C; q += 2) {
+          uint4 x, y;
+          ld_cg_v8(buf + u * C + q, x, y);
+          acc ^= x.x ^ x.y ^ x.z ^ x.w ^ y.x ^ y.y ^ y.z ^ y.w;
+        }
+      }
+    }
+  }
   if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);  // keeps the loads alive
+}
+
+using ProbeKernel = void (*)(uint4*, uint64_t, uint64_t, uint64_t, unsigned long long*);
+
+// Accesses in flight per thread that each mode is compiled for: reads keep
+// their data in registers until all INF have been issued (8 registers per
+// 32-byte read), so 32-byte reads stop at 16 and 64-byte reads at 8 (128
+// data registers), where no shape spills.  The kernels are compiled for
+// blocks of at most 256 threads and may use up to 255 registers
+// (__launch_bounds__(256, 1)): without that, the compiler keeps registers
+// few by consuming each read before issuing the next, and the requests in
+// flight are not the INF asked for.  Resident blocks per SM then follow from
+// the registers a shape needs.
+template <int MODE>
+static ProbeKernel probe_kernel_inf(int inf) {
+  constexpr int kMaxInf = MODE == 1 ? 8 : MODE == 0 ? 16 : 64;
+  switch (inf) {
+    case 1: return k_probe<MODE, 1>;
+    case 2: return k_probe<MODE, 2>;
+    case 4: return k_probe<MODE, 4>;
+    case 8: return k_probe<MODE, 8>;
+    case 16: return kMaxInf >= 16 ? k_probe<MODE, (kMaxInf >= 16 ? 16 : 1)> : nullptr;
+    case 32: return kMaxInf >= 32 ? k_probe<MODE, (kMaxInf >= 32 ? 32 : 1)> : nullptr;
+    case 64: return kMaxInf >= 64 ? k_probe<MODE, (kMaxInf >= 64 ? 64 : 1)> : nullptr;
+    default: return nullptr;
+  }
+}
+
+static ProbeKernel probe_kernel(int mode, int inf) {
+  switch (mode) {
+    case 0: return probe_kernel_inf<0>(inf);
+    case 1: return probe_kernel_inf<1>(inf);
+    case 2: return probe_kernel_inf<2>(inf);
+    case 3: return probe_kernel_inf<3>(inf);
+    case 4: return probe_kernel_inf<4>(inf);
+    case 5: return probe_kernel_inf<5>(inf);
+    case 6: return probe_kernel_inf<6>(inf);
+    case 7: return probe_kernel_inf<7>(inf);
+    case 8: return probe_kernel_inf<8>(inf);
+    default: return nullptr;
+  }
 }
 
 }  // namespace vss
 
 using namespace vss;
 
-extern "C" ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_access, int mode,
-                                      void* stream, float* ms) {
-  if (!buf_dev || !ms || mode < 0 || mode > 7 || (reinterpret_cast<uintptr_t>(buf_dev) & 255u))
+extern "C" ht_status vss_probe_random_cfg(void* buf_dev, uint64_t bytes, uint64_t n_access, int mode,
+                                          int inflight, int blocks_per_sm, int threads, void* stream,
+                                          float* ms) {
+  if (inflight == 0) inflight = 8;
+  if (blocks_per_sm == 0) blocks_per_sm = 8;
+  if (threads == 0) threads = 256;
+  if (!buf_dev || !ms || mode < 0 || mode > 8 || (reinterpret_cast<uintptr_t>(buf_dev) & 255u))
     return HT_ERR_INVALID;
+  if (blocks_per_sm < 1 || blocks_per_sm > 64 || threads < 32 || threads > 1024 || (threads & 31))
+    return HT_ERR_INVALID;
+  const ProbeKernel kern = probe_kernel(mode, inflight);
+  if (!kern) return HT_ERR_INVALID;
+  if (threads > 256) return HT_ERR_INVALID;  // the kernels' launch bound
   const uint64_t unit = (mode == 1) ? 64 : 32;
   const uint64_t n_units = bytes / unit;
   if (n_units < 1024 || n_access == 0) return HT_ERR_INVALID;
@@ -105,20 +191,10 @@ extern "C" ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_
   cudaEvent_t e0, e1;
   VSS_CUDA_TRY(cudaEventCreate(&e0));
   VSS_CUDA_TRY(cudaEventCreate(&e1));
-  const int blocks = sms * 8;
   uint4* b = static_cast<uint4*>(buf_dev);
   const uint64_t n_use = n_units - 1;  // keep the sink unit out of the random range
   VSS_CUDA_TRY(cudaEventRecord(e0, s));
-  switch (mode) {
-    case 0: k_probe<0><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
-    case 1: k_probe<1><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
-    case 2: k_probe<2><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
-    case 3: k_probe<3><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
-    case 4: k_probe<4><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
-    case 5: k_probe<5><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
-    case 6: k_probe<6><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
-    default: k_probe<7><<<blocks, 256, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink); break;
-  }
+  kern<<<sms * blocks_per_sm, threads, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink);
   VSS_CUDA_TRY(cudaGetLastError());
   VSS_CUDA_TRY(cudaEventRecord(e1, s));
   VSS_CUDA_TRY(cudaEventSynchronize(e1));
@@ -126,4 +202,10 @@ extern "C" ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return HT_OK;
+}
+
+extern "C" ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_access, int mode,
+                                      void* stream, float* ms) {
+  if (mode < 0 || mode > 7) return HT_ERR_INVALID;
+  return vss_probe_random_cfg(buf_dev, bytes, n_access, mode, 8, 8, 256, stream, ms);
 }

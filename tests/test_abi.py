@@ -66,6 +66,10 @@ def test_invalid_arguments_return_before_any_device_call(lib):
     assert lib.ht_create(2, 16, None, ctypes.byref(h)) == binding.HT_ERR_INVALID
     assert lib.ht_find_or_put(None, None, 0, None, None, None) == binding.HT_ERR_INVALID
     assert lib.reach_ctx_run(None, 0, None) == binding.HT_ERR_INVALID
+    ms = ctypes.c_float()
+    assert lib.vss_probe_random_cfg(None, 1 << 30, 1 << 20, 0, 8, 8, 256, None,
+                                    ctypes.byref(ms)) == binding.HT_ERR_INVALID
+    assert lib.vss_probe_random(None, 1 << 30, 1 << 20, 8, None, ctypes.byref(ms)) == binding.HT_ERR_INVALID
     assert lib.ht_status_string(binding.HT_ERR_FULL).decode().startswith("table full")
 
 
