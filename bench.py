@@ -12,7 +12,12 @@ variables in [0,4), a critical-state mutex, 16-word (64 B) state vectors,
 Prints ONE JSON line on rank 0.  `value` = states/s over the K timed steps
 (device-resident inputs, CUDA events around the steps), `e2e` = the same
 metric through the public C-ABI call reach() with host buffers (model upload,
-run, result download inside the timed region).  `--impl reference` times the
+run, result download inside the timed region).  The same line carries, under
+"configs", the other workloads measured in the same run: the tiny
+interleaving model, the hash-table benchmark's headline fill with default and
+autotuned parameters, the 256-model batch against one model per launch, and
+the served Poisson stream (p50/p99 latency, aggregate states/s) against each
+job alone (skip them with --no-extra-configs).  `--impl reference` times the
 CPU oracle on a bounded sample of the same workload instead.
 Under torchrun (N > 1) every rank runs its own replica (no data-path
 collective); value = all ranks' states / max over ranks of the time.
@@ -49,14 +54,42 @@ WORKLOADS = {
 }
 LOG2_BUCKETS = 26
 MAX_LEVELS = 1 << 14
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the workload's
-# kernel (ncu, 1 pass): k_reach_persistent on the full BEEM-shaped workload
-# (profiles/k_reach_persistent_beem-shaped.md), k_reach_batch on the 256
-# batched models (profiles/k_reach_batch_batched-256.md) and
-# k_find_or_put_stream on one 2^26-bucket fill at load 0.75, uniform reuse,
-# default parameters (profiles/k_find_or_put_stream_hashtable-fill.md).  Must be re-measured
-# (or set to None) whenever the kernel changes.
-NCU_TRAFFIC_BYTES = {"beem": 24.47e9, "batch256": 75.71e9, "hashtable-26-0.75-uniform-fused": 22.33e9}
+# DRAM traffic of a kernel (dram__bytes_read.sum + dram__bytes_write.sum, ncu,
+# one launch of a small case of the workload) per unit of work, with the hash
+# of the kernel sources the capture ran: kernel -> {"unit": ..., "bytes_per_unit":
+# ..., "sources_sha": ..., "capture": ...}.  A line reports it (scaled to the
+# run's units) only while the sources still hash the same; otherwise traffic is
+# null and the line says why.
+RECORDED_TRAFFIC: dict = {}
+
+
+def kernel_sources_sha() -> str:
+    """sha256 (first 16 hex digits) of the CUDA sources and the C-ABI header."""
+    import glob
+    import hashlib
+    pkg = os.path.join(ROOT, "paper_1004_2772_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(pkg, "*.cu")) + glob.glob(os.path.join(pkg, "*.cuh"))
+                   + glob.glob(os.path.join(pkg, "*.h"))) + [os.path.join(ROOT, "include", "reach.h")]
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str, units: float):
+    """(traffic bytes for `units` units of work or None, a note on its source)."""
+    rec = RECORDED_TRAFFIC.get(kernel)
+    sha = kernel_sources_sha()
+    if rec is None:
+        return None, {"kernel_sources_sha": sha, "note": "no DRAM capture recorded for this kernel"}
+    if rec["sources_sha"] != sha:
+        return None, {"kernel_sources_sha": sha, "capture_sources_sha": rec["sources_sha"],
+                      "note": "the kernel sources changed since the DRAM capture"}
+    return rec["bytes_per_unit"] * units, {"kernel_sources_sha": sha, "unit": rec["unit"],
+                                           "bytes_per_unit": rec["bytes_per_unit"],
+                                           "capture": rec["capture"]}
 
 
 def workload_model(name="beem"):
@@ -261,6 +294,8 @@ def main():
     ap.add_argument("--mode", default="persistent", choices=["persistent", "per-level", "graph"])
     ap.add_argument("--line-buckets", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra-configs", action="store_true",
+                    help="skip the tiny / hash-table / batch / served measurements of the default line")
     ap.add_argument("--workload", default="beem", choices=sorted(WORKLOADS))
     ap.add_argument("--log2-buckets", type=int, default=0, help="0 = the workload's size")
     ap.add_argument("--load-factor", type=float, default=0.75, help="hashtable: keys / buckets")
@@ -289,7 +324,8 @@ def main():
          "serve": run_serve, "probe-sweep": run_probe_sweep}[args.workload](args, world, rank, local, dev)
         return
 
-    # random-access rates of this GPU (the random-sector roofline's denominators)
+    # random-access rates of this GPU (the random-sector roofline's denominators):
+    # each mode's plateau over the probe shapes
     rates = binding.random_access_rates(gib=16, n_access=1 << 28)
     model = workload_model(args.workload)
     mode = {"persistent": binding.REACH_PERSISTENT, "per-level": binding.REACH_PER_LEVEL,
@@ -346,6 +382,9 @@ def main():
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     h2d = model.nbytes()
     d2h = 64 + 64 + 8 * len(r.level_sizes)
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
 
     peak, which = peaks()
     tab_bytes = binding.ht_bytes(LOG2_BUCKETS, model.state_words)
@@ -357,6 +396,8 @@ def main():
                    "steps: a latency-bound configuration")
     alg = algorithmic_bytes(got.states, got.transitions, model.state_words)
     achieved = alg / (kernel_ms / 1000.0) / 1e9
+    kname = {0: "k_reach_persistent", 1: "k_reach_level", 2: "k_reach_step"}[mode]
+    traffic, traffic_src = recorded_traffic(f"{kname}:{args.workload}", got.transitions)
     line = {
         "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max,
@@ -369,10 +410,9 @@ def main():
                    "l2": l2_note},
         "find_or_put_ops_per_s": trans_all / (t_max / 1000.0),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak,
-                     "traffic": (NCU_TRAFFIC_BYTES.get(args.workload) if mode == 0 else None),
-                     "kernel": {0: "k_reach_persistent", 1: "k_reach_level", 2: "k_reach_step"}[mode],
-                     "kernel_ms": kernel_ms, "algorithmic_bytes": alg, "peak_source": which},
+                     "frac": achieved / peak, "traffic": traffic, "traffic_source": traffic_src,
+                     "kernel": kname, "kernel_ms": kernel_ms, "algorithmic_bytes": alg,
+                     "peak_source": which},
         "random_roofline": random_roofline(got.states, got.transitions, kernel_ms, rates, peak,
                                            model.state_words),
         "e2e": {"value": states_all / (e2e_ms / 1000.0), "unit": "states/s",
@@ -380,16 +420,16 @@ def main():
         "gpu_launches": launches * args.steps,
         "clocks": clocks.summary(),
     }
+    if not args.no_extra_configs and args.workload == "beem" and mode == binding.REACH_PERSISTENT:
+        line["configs"] = extra_configs(args, world, local, dev, rates)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(model)
         line["cpu_baseline"]["host_cores_available"] = os.cpu_count()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-
 
 
 def base_line(args, world, metric, value, unit, ms_per_step, config, higher=True):
@@ -399,68 +439,122 @@ def base_line(args, world, metric, value, unit, ms_per_step, config, higher=True
             "config": config}
 
 
-def run_hashtable(args, world, rank, local, dev):
-    """Hash-table benchmark: one step = one fill of a 2^n table to the load
-    factor (2 * LF * 2^n find-or-put calls, half of them repeating an earlier
-    key uniformly or by Zipf(1.1)); value = find-or-put calls per second."""
+def probe_rates_dict(rates):
+    return {"read32": rates[0], "read64": rates[1], "write32": rates[2], "atomic32": rates[3]}
+
+
+# ---------------------------------------------------------------------------
+# The other workloads, as functions returning a result dict (used both by
+# their own --workload lines and by the default line's "configs").
+# ---------------------------------------------------------------------------
+
+def tiny_stats(steps, local):
+    """The tiny interleaving model (10^5 states, 2^18 buckets, L2-resident):
+    the three level drivers; value = states/s of the persistent driver."""
     import torch
-    from paper_1004_2772_gb300 import autotune, binding, synth
-    log2, lf = LOG2_BUCKETS, args.load_factor
+    from paper_1004_2772_gb300 import binding
+    m = synth.tiny_interleaving_model()
+    ctx = binding.ReachContext(18, m.state_words, max_levels=MAX_LEVELS)
+    ctx.load(m)
+    out = {"workload": m.name, "unit": "states/s"}
+    with ClockSampler(local) as clocks:
+        for name, mode in (("persistent", binding.REACH_PERSISTENT), ("graph", binding.REACH_GRAPH),
+                           ("per_level", binding.REACH_PER_LEVEL)):
+            for _ in range(3):
+                ctx.run(mode)
+            ref = ctx.result()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(steps):
+                ctx.run(mode)
+            e1.record()
+            torch.cuda.synchronize()
+            got = ctx.result()
+            assert (got.states, got.digest, got.level_sizes) == (ref.states, ref.digest, ref.level_sizes)
+            out[f"{name}_ms_per_run"] = e0.elapsed_time(e1) / steps
+    ctx.close()
+    out["value"] = got.states / (out["persistent_ms_per_run"] / 1e3)
+    out["states"], out["levels"] = got.states, len(got.level_sizes)
+    out["l2"] = "L2-resident (6 MB table), not flushed: latency-bound"
+    out["clocks"] = clocks.summary()
+    return out
+
+
+def hashtable_point(log2, lf, dist, key_mode, params, steps, warmup, rates, local):
+    """One fill of a 2^log2 table to load factor lf per step (2 * lf * 2^log2
+    find-or-put calls, half of them repeating an earlier key uniformly or by
+    Zipf(1.1)); value = find-or-put calls per second."""
+    import torch
+    from paper_1004_2772_gb300 import binding
     n_ids = int(lf * (1 << log2))
     calls = 2 * n_ids
-    zipf = synth.zipf_table(n_ids) if args.dist == "zipf" else None
-    params = {"line_buckets": args.line_buckets}
-    tuned = None
-    if args.autotune:
-        tuned = autotune.tune_table(log2, lf, args.dist, cache_path=None)
-        params = dict(tuned["best"])
-    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
+    zipf = synth.zipf_table(n_ids) if dist == "zipf" else None
     tab = binding.Table(log2, 16, **params)
     tab_gb = binding.ht_bytes(log2, 16) / 1e9
-    keys = None
-    if args.key_mode == "api":
-        keys = tab.gen_keys(1, n_ids, 0, calls, zipf)
+    keys = tab.gen_keys(1, n_ids, 0, calls, zipf) if key_mode == "api" else None
+
     def step():
         tab.clear()
         if keys is None:
             return tab.find_or_put_stream(1, n_ids, 0, calls, zipf, sync=False)
         return tab.find_or_put(keys, want_idx=True)
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         step()
     torch.cuda.synchronize()
-    barrier(world)
     with ClockSampler(local) as clocks:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
-            out = step()
+        for _ in range(steps):
+            step()
         e1.record()
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     # the last fill must have stored exactly the fill's distinct keys
     st = tab.stats()
     assert st.stored == n_ids and st.error == 0, (st.stored, n_ids)
-    t_max = max_over_ranks(ms, world, dev)
-    ops = sum_over_ranks(float(calls), world, dev) / (t_max / 1e3)
+    tab.close()
+    del keys
+    torch.cuda.empty_cache()
     dup, new = calls - n_ids, n_ids
-    alg = calls * 32 + dup * 64 + new * (64 + 32) + (calls * (64 + 5) if keys is not None else 0)
+    alg = calls * 32 + dup * 64 + new * (64 + 32) + (calls * (64 + 5) if key_mode == "api" else 0)
+    bound_s = hashtable_bound_s(calls, n_ids, rates, key_mode == "api")
     peak, which = peaks()
-    bound_s = calls / rates[0] + dup / rates[1] + 3 * new / rates[2]
+    kname = "k_find_or_put_stream" if key_mode == "fused" else "k_find_or_put"
+    traffic, src = (recorded_traffic(f"{kname}:{log2}-{lf}-{dist}", calls) if not params
+                    else (None, {"note": "no DRAM capture recorded for these parameters"}))
+    return {"workload": f"hashtable-W16-2^{log2}-lf{lf}-{dist}-{key_mode}", "value": calls / (ms / 1e3),
+            "unit": "find_or_put/s", "ms_per_fill": ms, "calls_per_fill": calls, "distinct_keys": n_ids,
+            "params": params, "steps": steps,
+            "l2": f"inputs larger than L2 (table {tab_gb:.1f} GB)",
+            "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": traffic, "traffic_source": src,
+                         "kernel": kname, "algorithmic_bytes": alg, "peak_source": which},
+            "random_roofline": {"bound_ms": bound_s * 1e3, "frac": bound_s * 1e3 / ms,
+                                "probe_rates_per_s": probe_rates_dict(rates)},
+            "gpu_launches": steps * (1 if key_mode == "fused" else 1),
+            "clocks": clocks.summary()}
+
+
+def run_hashtable(args, world, rank, local, dev):
+    """Hash-table benchmark: one step = one fill (hashtable_point)."""
+    from paper_1004_2772_gb300 import autotune, binding
+    params = {"line_buckets": args.line_buckets} if args.line_buckets != 32 else {}
+    tuned = None
+    if args.autotune:
+        tuned = autotune.tune_table(LOG2_BUCKETS, args.load_factor, args.dist, cache_path=None)
+        params = dict(tuned["best"])
+    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
+    r = hashtable_point(LOG2_BUCKETS, args.load_factor, args.dist, args.key_mode, params, args.steps,
+                        args.warmup, rates, local)
+    t_max = max_over_ranks(r["ms_per_fill"], world, dev)
+    ops = sum_over_ranks(float(r["calls_per_fill"]), world, dev) / (t_max / 1e3)
     line = base_line(args, world, "find_or_put ops/sec on 1 GB300 (hash-table benchmark)", ops,
                      "find_or_put/s", t_max,
-                     {"workload": f"hashtable-W16-2^{log2}-lf{lf}-{args.dist}-{args.key_mode}",
-                      "calls_per_step": calls, "distinct_keys": n_ids, "params": params,
-                      "l2": f"inputs larger than L2 (table {tab_gb:.1f} GB)"})
-    line["roofline"] = {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak,
-                        "unit": "GB/s", "frac": alg / (ms / 1e3) / 1e9 / peak,
-                        "traffic": (None if tuned or args.line_buckets != 32 else NCU_TRAFFIC_BYTES.get(
-                            f"hashtable-{log2}-{lf}-{args.dist}-{args.key_mode}")),
-                        "algorithmic_bytes": alg, "peak_source": which}
-    line["random_roofline"] = {"bound_ms": bound_s * 1e3, "frac": bound_s * 1e3 / ms,
-                               "probe_rates_per_s": {"read32": rates[0], "read64": rates[1],
-                                                     "write32": rates[2], "atomic32": rates[3]}}
-    line["gpu_launches"] = args.steps * (1 if keys is None else 1)
-    line["clocks"] = clocks.summary()
+                     {"workload": r["workload"], "calls_per_step": r["calls_per_fill"],
+                      "distinct_keys": r["distinct_keys"], "params": params, "l2": r["l2"]})
+    for k in ("roofline", "random_roofline", "gpu_launches", "clocks"):
+        line[k] = r[k]
     if tuned:
         line["autotune"] = {"best": tuned["best"], "candidates": len(tuned["all"])}
     if rank == 0:
@@ -543,159 +637,224 @@ def run_hashtable_sweep(args, world, rank, local, dev):
         print(json.dumps(line), flush=True)
 
 
-def run_batch(args, world, rank, local, dev):
-    """Batched reachability: one step = the 256 seeded interleaving models of
-    uneven size (3-12 processes, 8-32 words, 10^3-10^6 states) in one
-    persistent launch replayed as a CUDA graph; compared with one model per
-    launch."""
+def batch_stats(models, steps, warmup, rates, local):
+    """The batched models in one persistent launch replayed as a CUDA graph
+    (value = states/s), against one model per launch through reach() (each
+    model alone, on a context sized for it)."""
     import torch
-    from paper_1004_2772_gb300 import binding, synth
-    models = synth.batched_models(count=args.models, first_seed=1)
-    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
+    from paper_1004_2772_gb300 import binding
     bt = binding.ReachBatch(models, max_levels=4096)
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         bt.run(use_graph=True)
     ref, grows, st = bt.results()
     assert st == 0
-    barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(args.steps):
+        for _ in range(steps):
             bt.run(use_graph=True)
         e1.record()
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = e0.elapsed_time(e1) / steps
     got, grows, st = bt.results()
     assert st == 0 and [r.digest for r in got] == [r.digest for r in ref]
+    bt.close()
+    del bt
+    torch.cuda.empty_cache()
     states = sum(r.states for r in got)
-    # one model per launch (the plain path), contexts sized per model
-    ctxs, t0 = {}, time.perf_counter()
+    # one model per launch (the plain path), contexts sized per model; device
+    # time of each run from the library's events, and the host wall time
+    ctxs, dev_ms, t0 = {}, 0.0, time.perf_counter()
     for m in models:
         lg = max(10, int(np.ceil(np.log2(float(np.prod(m.n_local)) / 0.5))))
         ctxs.setdefault(lg, binding.ReachContext(lg, 32, max_levels=4096))
-        ctxs[lg].reach(m)
+        r = ctxs[lg].reach(m)
+        assert r.status == 0
+        dev_ms += ctxs[lg].last_timing()[0]
     torch.cuda.synchronize()
     loop_ms = (time.perf_counter() - t0) * 1e3
-    t_max = max_over_ranks(ms, world, dev)
-    value = sum_over_ranks(float(states), world, dev) / (t_max / 1e3)
-    line = base_line(args, world, f"states/sec on 1 GB300 (batched reachability, {len(models)} models)",
-                     value, "states/s", t_max,
-                     {"workload": f"batched-{len(models)}-interleaving-models", "models": len(models),
-                      "states": states, "table_grows": int(sum(grows)), "graph": True,
-                      "l2": "inputs larger than L2 (tables and frontiers, GBs)"})
-    line["one_model_per_launch"] = {"ms": loop_ms, "states_per_s": states / (loop_ms / 1e3)}
-    # the batch kernel is the only kernel of a step: its event time is the step time
+    for c in ctxs.values():
+        c.close()
+    del ctxs
+    torch.cuda.empty_cache()
     peak, which = peaks()
     alg = sum(algorithmic_bytes(r.states, r.transitions, m.state_words) for m, r in zip(models, got))
     bound_s = sum(random_bound_s(r.states, r.transitions, rates, peak, m.state_words)
                   for m, r in zip(models, got))
     fops = sum(r.transitions for r in got)
-    line["find_or_put_ops_per_s"] = fops / (ms / 1e3)
-    line["roofline"] = {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                        "frac": alg / (ms / 1e3) / 1e9 / peak,
-                        "traffic": NCU_TRAFFIC_BYTES.get(f"batch{len(models)}"),
-                        "kernel": "k_reach_batch", "algorithmic_bytes": alg, "peak_source": which}
-    line["random_roofline"] = {"bound_ms": bound_s * 1e3, "kernel_ms": ms, "frac": bound_s * 1e3 / ms,
-                               "probe_rates_per_s": {"read32": rates[0], "read64": rates[1],
-                                                     "write32": rates[2], "atomic32": rates[3]},
-                               "unit": "fraction of the random-access bound (probe-measured rates)"}
-    line["gpu_launches"] = args.steps
-    line["clocks"] = clocks.summary()
+    traffic, src = recorded_traffic(f"k_reach_batch:batch{len(models)}", fops)
+    return {"workload": f"batched-{len(models)}-interleaving-models", "value": states / (ms / 1e3),
+            "unit": "states/s", "ms_per_batch": ms, "models": len(models), "states": states,
+            "table_grows": int(sum(grows)), "graph": True, "steps": steps,
+            "l2": "inputs larger than L2 (tables and frontiers, GBs)",
+            "find_or_put_ops_per_s": fops / (ms / 1e3),
+            "one_model_per_launch": {"wall_ms": loop_ms, "device_ms": dev_ms,
+                                     "states_per_s": states / (loop_ms / 1e3),
+                                     "batch_speedup_vs_wall": loop_ms / ms},
+            "roofline": {"bound": "hbm", "achieved": alg / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (ms / 1e3) / 1e9 / peak, "traffic": traffic, "traffic_source": src,
+                         "kernel": "k_reach_batch", "algorithmic_bytes": alg, "peak_source": which},
+            "random_roofline": {"bound_ms": bound_s * 1e3, "kernel_ms": ms, "frac": bound_s * 1e3 / ms,
+                                "probe_rates_per_s": probe_rates_dict(rates),
+                                "unit": "fraction of the random-access bound (probe-measured rates)"},
+            "gpu_launches": steps, "clocks": clocks.summary()}
+
+
+def run_batch(args, world, rank, local, dev):
+    """Batched reachability: one step = the 256 seeded interleaving models of
+    uneven size (3-12 processes, 8-32 words, 10^3-10^6 states) in one
+    persistent launch replayed as a CUDA graph; compared with one model per
+    launch."""
+    from paper_1004_2772_gb300 import binding
+    models = synth.batched_models(count=args.models, first_seed=1)
+    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
+    r = batch_stats(models, args.steps, args.warmup, rates, local)
+    t_max = max_over_ranks(r["ms_per_batch"], world, dev)
+    value = sum_over_ranks(float(r["states"]), world, dev) / (t_max / 1e3)
+    line = base_line(args, world, f"states/sec on 1 GB300 (batched reachability, {len(models)} models)",
+                     value, "states/s", t_max,
+                     {"workload": r["workload"], "models": r["models"], "states": r["states"],
+                      "table_grows": r["table_grows"], "graph": True, "l2": r["l2"]})
+    for k in ("one_model_per_launch", "find_or_put_ops_per_s", "roofline", "random_roofline",
+              "gpu_launches", "clocks"):
+        line[k] = r[k]
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def serve_stats(jobs, slots_list, plain, local):
+    """The served stream submitted in real time (arrival times of `jobs`) to a
+    server of each slot count (HBM budget = 85% of free memory): aggregate
+    states/s, p50/p99 latency; with `plain`, each job alone through reach()
+    in arrival order (device time of each run, host overheads excluded)."""
+    import torch
+    from paper_1004_2772_gb300 import binding
+    free, _ = torch.cuda.mem_get_info()
+    out = {}
+    with ClockSampler(local) as clocks:
+        for slots in slots_list:
+            srv = binding.Server(budget_bytes=int(free * 0.85), n_slots=slots, max_levels=4096)
+            srv.submit(jobs[0][1])
+            while not srv.poll(want_levels=False):
+                time.sleep(0.001)
+            done, k, t0 = [], 0, time.perf_counter()
+            while len(done) < len(jobs):
+                now = time.perf_counter() - t0
+                while k < len(jobs) and jobs[k][0] <= now:
+                    srv.submit(jobs[k][1])
+                    k += 1
+                done += srv.poll(want_levels=False)
+                time.sleep(0.0005)
+            span = time.perf_counter() - t0
+            lat = np.array([d.latency_s for d in done]) * 1e3
+            queue = np.array([d.admit_s - d.submit_s for d in done]) * 1e3
+            run = np.array([d.done_s - d.admit_s for d in done]) * 1e3
+            size = np.array([d.result.states for d in done], dtype=np.float64)
+            assert all(d.result.status == 0 for d in done)
+            by_size = {}
+            for lo, hi in ((1e4, 1e5), (1e5, 1e6), (1e6, 1e7), (1e7, 1e9)):
+                sel = (size >= lo) & (size < hi)
+                if sel.any():
+                    by_size[f"{lo:.0e}-{hi:.0e}"] = {"jobs": int(sel.sum()),
+                                                      "p50_ms": float(np.percentile(lat[sel], 50))}
+            out[slots] = {"span_s": span, "states": int(size.sum()),
+                          "states_per_s": float(size.sum()) / span,
+                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "max_ms": float(lat.max()), "kernel_launches": srv.status()["kernel_launches"],
+                          "queue_p50_ms": float(np.percentile(queue, 50)),
+                          "run_p50_ms": float(np.percentile(run, 50)), "p50_ms_by_states": by_size}
+            srv.close()
+            del srv
+            torch.cuda.empty_cache()
+    if plain:
+        # the plain path: each job alone through reach() on a context sized for
+        # it, in arrival order (a job starts when it has arrived and the
+        # previous one finished)
+        ctxs, t_free, lat_plain = {}, 0.0, []
+        for arrival, m in jobs:
+            bound = float(np.prod(np.asarray(m.n_local, dtype=np.float64)))
+            lg = max(10, int(np.ceil(np.log2(bound / 0.5))))
+            ctx = ctxs.get(lg) or binding.ReachContext(lg, m.state_words, max_levels=4096)
+            r = ctx.reach(m)
+            assert r.status == 0
+            run_s = ctx.last_timing()[0] / 1e3
+            start = max(arrival, t_free)
+            t_free = start + run_s
+            lat_plain.append((t_free - arrival) * 1e3)
+            if lg <= 24:
+                ctxs[lg] = ctx
+            else:
+                ctx.close()
+                del ctx
+                torch.cuda.empty_cache()
+        for ctx in ctxs.values():
+            ctx.close()
+        del ctxs
+        torch.cuda.empty_cache()
+        lat_plain = np.array(lat_plain)
+        out["plain"] = {"p50_ms": float(np.percentile(lat_plain, 50)),
+                        "p99_ms": float(np.percentile(lat_plain, 99)),
+                        "note": "device time of each job alone via reach(), queued in arrival order; "
+                                "host overheads excluded"}
+    out["clocks"] = clocks.summary()
+    return out
 
 
 def run_serve(args, world, rank, local, dev):
     """Served reachability: a Poisson stream (20 jobs/s) of interleaving jobs of
     log-uniform size 10^4..2*10^8 states (W = 16) submitted in real time to the
-    server (HBM budget = 85% of free memory; a job that finds the GPU idle runs
-    on the single-model kernel, queues go to the continuous-batching kernel);
-    reports aggregate states/s and p50/p99 latency, the same stream with one
-    slot, and each job alone through reach() in arrival order."""
-    import torch
-    from paper_1004_2772_gb300 import binding, synth
+    server (a job that finds the GPU idle runs on the single-model kernel,
+    queues go to the continuous-batching kernel); reports aggregate states/s
+    and p50/p99 latency, the same stream with one slot, and each job alone
+    through reach() in arrival order."""
     jobs = synth.served_jobs(seed=5, rate=20.0, duration_s=args.duration)
-    free, _ = torch.cuda.mem_get_info()
-    out = {}
-    for slots in (64, 1):
-        srv = binding.Server(budget_bytes=int(free * 0.85), n_slots=slots, max_levels=4096)
-        srv.submit(jobs[0][1])
-        while not srv.poll(want_levels=False):
-            time.sleep(0.001)
-        done, k, t0 = [], 0, time.perf_counter()
-        while len(done) < len(jobs):
-            now = time.perf_counter() - t0
-            while k < len(jobs) and jobs[k][0] <= now:
-                srv.submit(jobs[k][1])
-                k += 1
-            done += srv.poll(want_levels=False)
-            time.sleep(0.0005)
-        span = time.perf_counter() - t0
-        lat = np.array([d.latency_s for d in done]) * 1e3
-        queue = np.array([d.admit_s - d.submit_s for d in done]) * 1e3
-        run = np.array([d.done_s - d.admit_s for d in done]) * 1e3
-        size = np.array([d.result.states for d in done], dtype=np.float64)
-        assert all(d.result.status == 0 for d in done)
-        by_size = {}
-        for lo, hi in ((1e4, 1e5), (1e5, 1e6), (1e6, 1e7), (1e7, 1e9)):
-            sel = (size >= lo) & (size < hi)
-            if sel.any():
-                by_size[f"{lo:.0e}-{hi:.0e}"] = {"jobs": int(sel.sum()),
-                                                  "p50_ms": float(np.percentile(lat[sel], 50))}
-        out[slots] = {"span_s": span, "states": sum(d.result.states for d in done),
-                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                      "max_ms": float(lat.max()), "kernel_launches": srv.status()["kernel_launches"],
-                      "queue_p50_ms": float(np.percentile(queue, 50)),
-                      "run_p50_ms": float(np.percentile(run, 50)), "p50_ms_by_states": by_size}
-        srv.close()
-        del srv
-        torch.cuda.empty_cache()
-    # the plain path: each job alone through reach() on a context sized for it,
-    # in arrival order (a job starts when it has arrived and the previous one
-    # finished; device time of each run from the library's events)
-    ctxs, t_free, lat_plain = {}, 0.0, []
-    for arrival, m in jobs:
-        bound = float(np.prod(np.asarray(m.n_local, dtype=np.float64)))
-        lg = max(10, int(np.ceil(np.log2(bound / 0.5))))
-        ctx = ctxs.get(lg) or binding.ReachContext(lg, m.state_words, max_levels=4096)
-        r = ctx.reach(m)
-        assert r.status == 0
-        run_s = ctx.last_timing()[0] / 1e3
-        start = max(arrival, t_free)
-        t_free = start + run_s
-        lat_plain.append((t_free - arrival) * 1e3)
-        if lg <= 24:
-            ctxs[lg] = ctx
-        else:
-            ctx.close()
-            del ctx
-            torch.cuda.empty_cache()
-    for ctx in ctxs.values():
-        ctx.close()
-    del ctxs
-    torch.cuda.empty_cache()
-    lat_plain = np.array(lat_plain)
+    out = serve_stats(jobs, (64, 1), True, local)
     c = out[64]
     line = base_line(args, world, "states/sec on 1 GB300 (served reachability, Poisson 20 jobs/s)",
-                     c["states"] / c["span_s"], "states/s", c["span_s"] * 1e3 / max(1, len(jobs)),
+                     c["states_per_s"], "states/s", c["span_s"] * 1e3 / max(1, len(jobs)),
                      {"workload": f"served-poisson20-{len(jobs)}jobs-1e4..2e8-W16", "slots": 64,
                       "jobs": len(jobs)})
     line["latency_ms"] = {"p50": c["p50_ms"], "p99": c["p99_ms"], "max": c["max_ms"],
                           "queue_p50": c["queue_p50_ms"], "run_p50": c["run_p50_ms"],
                           "p50_by_states": c["p50_ms_by_states"]}
-    line["one_job_at_a_time"] = {"p50_ms": out[1]["p50_ms"], "p99_ms": out[1]["p99_ms"],
-                                 "queue_p50_ms": out[1]["queue_p50_ms"],
-                                 "run_p50_ms": out[1]["run_p50_ms"],
-                                 "p50_by_states": out[1]["p50_ms_by_states"],
-                                 "states_per_s": out[1]["states"] / out[1]["span_s"]}
-    line["plain_reach_in_arrival_order"] = {"p50_ms": float(np.percentile(lat_plain, 50)),
-                                            "p99_ms": float(np.percentile(lat_plain, 99)),
-                                            "note": "device time of each job alone via reach(), queued in arrival order; host overheads excluded"}
+    o = out[1]
+    line["one_job_at_a_time"] = {"p50_ms": o["p50_ms"], "p99_ms": o["p99_ms"],
+                                 "queue_p50_ms": o["queue_p50_ms"], "run_p50_ms": o["run_p50_ms"],
+                                 "p50_by_states": o["p50_ms_by_states"], "states_per_s": o["states_per_s"]}
+    line["plain_reach_in_arrival_order"] = out["plain"]
     line["gpu_launches"] = c["kernel_launches"]
+    line["clocks"] = out["clocks"]
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def extra_configs(args, world, local, dev, rates):
+    """The default line's other workloads (one GPU each, rank 0's numbers)."""
+    from paper_1004_2772_gb300 import autotune
+    out = {"tiny": tiny_stats(max(10, args.steps), local)}
+    steps = max(5, min(args.steps, 20))
+    out["hashtable"] = hashtable_point(26, 0.75, "uniform", "fused", {}, steps, args.warmup, rates, local)
+    t0 = time.perf_counter()
+    tuned = autotune.tune_table(26, 0.75, "uniform", cache_path=None)
+    tune_s = time.perf_counter() - t0
+    ht = hashtable_point(26, 0.75, "uniform", "fused", dict(tuned["best"]), steps, args.warmup, rates,
+                         local)
+    ht["autotune"] = {"best": tuned["best"], "candidates": len(tuned["all"]), "seconds": tune_s}
+    out["hashtable_autotuned"] = ht
+    out["batch"] = batch_stats(synth.batched_models(count=256, first_seed=1), max(3, min(args.steps, 10)),
+                               args.warmup, rates, local)
+    jobs = synth.served_jobs(seed=5, rate=20.0, duration_s=10.0)
+    sv = serve_stats(jobs, (64,), True, local)
+    c = sv[64]
+    out["serve"] = {"workload": f"served-poisson20-{len(jobs)}jobs-1e4..2e8-W16", "value": c["states_per_s"],
+                    "unit": "states/s", "slots": 64, "jobs": len(jobs), "span_s": c["span_s"],
+                    "latency_ms": {"p50": c["p50_ms"], "p99": c["p99_ms"], "max": c["max_ms"],
+                                   "queue_p50": c["queue_p50_ms"], "run_p50": c["run_p50_ms"],
+                                   "p50_by_states": c["p50_ms_by_states"]},
+                    "plain_reach_in_arrival_order": sv["plain"], "gpu_launches": c["kernel_launches"],
+                    "clocks": sv["clocks"]}
+    return out
 
 
 def run_probe_sweep(args, world, rank, local, dev):

@@ -61,26 +61,20 @@ __device__ __forceinline__ void vec_set(Vec<NV>& v, int i, uint32_t x) {
   }
 }
 
-// One round of a level, warp-cooperatively and load-balanced over successors.
-//
-// The warp expands frontier rows [base, base + spw) (spw <= 32).  Phase 1:
-// lane i < spw reads state i's row, keeps it (and its hash sum) in shared
-// memory, and lists the enabled edges of the state (next-state) as
-// descriptors (edge | process << 24) in its own slice of the warp's
-// descriptor area; it counts the state's transitions and, when there are
-// none, a deadlock.  A warp scan of the counts gives T successors.  Phase 2:
-// lane j, j+32, ... builds successor j from its owner's row and the
-// descriptor and runs find-or-put -- so no lane serialises a whole fan-out.
-// New states are appended to the next frontier (rows) with one atomicAdd per
-// warp and iteration, straight from registers.
+// Phase 1 of a round, warp-cooperatively: the warp takes frontier rows
+// [base, base + spw) (spw <= 32); lane i < spw reads state i's row, keeps it
+// (and its hash sum) in shared memory, and lists the enabled edges of the
+// state (next-state) as descriptors (edge | process << 24) in its own slice of
+// the warp's descriptor area; it counts the state's transitions and, when
+// there are none, a deadlock.  A warp scan of the counts gives the round's T
+// successors (returned; the inclusive prefix per lane stays in shared memory).
 // RT: rows have the table's run-time width t.nv (<= NV) instead of NV.
 // TR: record predecessors and the first deadlock (tr points to TraceDev).
-template <int NV, int L, bool RT, bool TR = false, int BW = 32>
-__device__ __forceinline__ void expand_round(const TableView& t, const SModel& m, const uint4* cur,
-                                             uint32_t n_cur, uint64_t base, uint32_t spw,
-                                             uint4* next, uint32_t* next_count, uint32_t cap,
-                                             Acc& acc, LocalCounters& lc, uint32_t* wsm,
-                                             const TraceDev* tr = nullptr) {
+template <int NV, bool RT, bool TR>
+__device__ __forceinline__ uint32_t round_successors(const TableView& t, const SModel& m,
+                                                     const uint4* cur, uint32_t n_cur, uint64_t base,
+                                                     uint32_t spw, Acc& acc, uint32_t* wsm,
+                                                     const TraceDev* tr) {
   constexpr int RS = row_stride<NV>();
   uint32_t* rows = wsm;
   uint32_t* desc = wsm + 32 * RS;
@@ -89,7 +83,6 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
   const int P = m.P;
   const int maxfan = m.maxfan;
   const uint32_t nvr = RT ? t.nv : (uint32_t)NV;
-  // ---- phase 1: expand the round's states into successor descriptors
   uint32_t c = 0;
   const uint64_t f = base + lane;
   if (lane < spw && f < n_cur) {
@@ -146,9 +139,64 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
   pref[lane] = incl;
   const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
   __syncwarp();
-  // ---- phase 2: one successor per lane per iteration; new states are
-  // appended to the next frontier (rows) with one atomicAdd per warp and
-  // iteration, straight from registers
+  return T;
+}
+
+// Successor j (< T) of the round listed by round_successors: its vector w and
+// table hash h, built from its owner's row and descriptor in shared memory
+// (the successor's hash sum from the parent's: only words p and P + upd_var
+// change); TR: the owner's bucket index too.
+template <int NV, bool TR>
+__device__ __forceinline__ void round_successor(const TableView& t, const SModel& m,
+                                                const uint32_t* wsm, uint32_t j, Vec<NV>& w,
+                                                uint64_t& h, uint32_t& parent_idx) {
+  constexpr int RS = row_stride<NV>();
+  const uint32_t* rows = wsm;
+  const uint32_t* desc = wsm + 32 * RS;
+  const uint32_t* pref = desc + kDescCap;
+  const int P = m.P;
+  uint32_t o = 0;  // owner = first lane whose inclusive prefix exceeds j
+#pragma unroll
+  for (uint32_t step = 16; step > 0; step >>= 1)
+    if (pref[o + step - 1] <= j) o += step;
+  const uint32_t k = j - (o ? pref[o - 1] : 0u);
+  const uint32_t dd = desc[o * m.maxfan + k];
+  const int e = (int)(dd & 0xFFFFFFu);
+  const int p = (int)(dd >> 24);
+  const int4 E = m.edges[e];
+  const uint32_t* ro = rows + o * RS;
+  const uint4* r = reinterpret_cast<const uint4*>(ro);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) w.c[q] = r[q];
+  uint64_t hs = (uint64_t)ro[4 * NV] | ((uint64_t)ro[4 * NV + 1] << 32);
+  hs += hash_term(t.seed, p, (uint32_t)E.x) - hash_term(t.seed, p, ro[p]);
+  vec_set(w, p, (uint32_t)E.x);
+  if (E.w >= 0) {
+    const int q = P + E.w;
+    const uint32_t uv = (uint32_t)m.uval[e];
+    hs += hash_term(t.seed, q, uv) - hash_term(t.seed, q, ro[q]);
+    vec_set(w, q, uv);
+  }
+  h = hash_final(hs, t.state_words);
+  if (TR) parent_idx = ro[4 * NV + 2];
+}
+
+// One round of a level, warp-cooperatively and load-balanced over successors.
+//
+// Phase 1 (round_successors) lists the round's T successors as descriptors.
+// Phase 2: lane j, j+32, ... builds successor j (round_successor) and runs
+// find-or-put -- so no lane serialises a whole fan-out.  New states are
+// appended to the next frontier (rows) with one atomicAdd per warp and
+// iteration, straight from registers.
+template <int NV, int L, bool RT, bool TR = false, int BW = 32>
+__device__ __forceinline__ void expand_round(const TableView& t, const SModel& m, const uint4* cur,
+                                             uint32_t n_cur, uint64_t base, uint32_t spw,
+                                             uint4* next, uint32_t* next_count, uint32_t cap,
+                                             Acc& acc, LocalCounters& lc, uint32_t* wsm,
+                                             const TraceDev* tr = nullptr) {
+  const unsigned lane = lane_id();
+  const uint32_t nvr = RT ? t.nv : (uint32_t)NV;
+  const uint32_t T = round_successors<NV, RT, TR>(t, m, cur, n_cur, base, spw, acc, wsm, tr);
   const uint32_t iters = (T + 31) / 32;
   for (uint32_t it = 0; it < iters; ++it) {
     const uint32_t j = it * 32 + lane;
@@ -158,33 +206,7 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
     const bool valid = j < T;
     uint64_t h = 0;
     uint32_t parent_idx = 0;
-    if (valid) {
-      uint32_t o = 0;  // owner = first lane whose inclusive prefix exceeds j
-#pragma unroll
-      for (uint32_t step = 16; step > 0; step >>= 1)
-        if (pref[o + step - 1] <= j) o += step;
-      const uint32_t k = j - (o ? pref[o - 1] : 0u);
-      const uint32_t dd = desc[o * maxfan + k];
-      const int e = (int)(dd & 0xFFFFFFu);
-      const int p = (int)(dd >> 24);
-      const int4 E = m.edges[e];
-      const uint32_t* ro = rows + o * RS;
-      const uint4* r = reinterpret_cast<const uint4*>(ro);
-#pragma unroll
-      for (int q = 0; q < NV; ++q) w.c[q] = r[q];
-      // successor hash from the parent's sum: only words p (and P + upd_var) change
-      uint64_t hs = (uint64_t)ro[4 * NV] | ((uint64_t)ro[4 * NV + 1] << 32);
-      hs += hash_term(t.seed, p, (uint32_t)E.x) - hash_term(t.seed, p, ro[p]);
-      vec_set(w, p, (uint32_t)E.x);
-      if (E.w >= 0) {
-        const int q = P + E.w;
-        const uint32_t uv = (uint32_t)m.uval[e];
-        hs += hash_term(t.seed, q, uv) - hash_term(t.seed, q, ro[q]);
-        vec_set(w, q, uv);
-      }
-      h = hash_final(hs, t.state_words);
-      if (TR) parent_idx = ro[4 * NV + 2];
-    }
+    if (valid) round_successor<NV, TR>(t, m, wsm, j, w, h, parent_idx);
     // Siblings share successors (diamonds), so equal successors often meet in
     // one iteration: the lowest such lane probes, the others confirm equality
     // word by word and take its answer as "seen" instead of waiting on a
