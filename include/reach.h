@@ -450,6 +450,64 @@ ht_status serve_status(serve_t* s, uint32_t* queued, uint32_t* running, uint64_t
 /* Stop accepting, wait for running jobs, release everything. */
 ht_status serve_close(serve_t* s);
 
+/* ------------------------------------------------------------------------ */
+/* Owner-partitioned reachability (static state-space partitioning).         */
+/* ------------------------------------------------------------------------ */
+
+/* The architecture that Sec. 4.1 describes for Spin and DiVinE 2, against
+ * which the paper sets its shared table: a breadth-first exploration in which
+ * a hash function assigns every successor to one worker, which checks it
+ * against its own state storage.  Here n_parts owner partitions on one GPU:
+ * owner(v) = the top log2(n_parts) bits of the state hash (so the memo of a
+ * partition's buckets carries log2(n_parts) fewer free bits).  Partition o has
+ * its own table of 2^log2_buckets_part buckets (the store of Sec. 3:
+ * find-or-put, 32-bit buckets, 128-byte lines) and its own frontier.  Each BFS
+ * level (Alg. "Reachability analysis") runs, over chunks of the frontier:
+ *   expand   all partitions' states with the shared-table drivers' successor
+ *            generator; successors and their hashes go to an outbox, counted
+ *            per (source partition, owner);
+ *   plan     the counts become receive offsets: owner o's inbox holds the
+ *            segments (0, o), (1, o), ... (n_parts-1, o) in order -- the
+ *            layout an all-to-all exchange between n_parts ranks delivers;
+ *   scatter  outbox rows to their inbox segments;
+ *   insert   each owner's find-or-put over its inbox, new states to its next
+ *            frontier.
+ * The results (states, transitions, deadlocks, level sizes, digest) equal
+ * reach() on one shared table.  exchange_rows bounds the rows of one chunk
+ * (outbox and inbox each hold that many; at least 960, at most 2^31).
+ * n_parts is 1, 2, 4, 8 or 16; log2_buckets_part in [10, 31];
+ * max_state_words in [1, 32].  Same ownership and error conventions as
+ * reach_ctx_*; params may be NULL and, when given, must keep 32-bit buckets,
+ * 128-byte lines and one lane per key. */
+typedef struct part_reach part_reach_t;
+
+ht_status part_reach_bytes(int n_parts, int log2_buckets_part, int max_state_words, uint64_t exchange_rows,
+                           uint64_t* bytes);
+/* mem_dev: 256-byte aligned, at least part_reach_bytes() bytes, kept alive by
+ * the caller until part_reach_destroy.  Synchronous. */
+ht_status part_reach_create_at(int n_parts, int log2_buckets_part, int max_state_words,
+                               uint64_t exchange_rows, const ht_params* params, void* mem_dev,
+                               uint64_t mem_bytes, part_reach_t** out);
+ht_status part_reach_destroy(part_reach_t* c);
+
+/* Explore from init (host model and init): clears every partition's table,
+ * runs all levels (the host reads each level's size; enqueued on `stream` and
+ * synchronous), and returns the result like reach().  part_states_host
+ * (n_parts entries, may be NULL): states owned by each partition;
+ * exchanged_host (may be NULL): successors sent to a partition other than the
+ * one that generated them.  HT_ERR_FULL: a partition's table overflowed;
+ * HT_ERR_LEVELS: more levels than max_levels. */
+ht_status part_reach_run(part_reach_t* c, const reach_model* m, const int32_t* init_host, void* stream,
+                         uint64_t* level_sizes_host, uint32_t max_levels, reach_result* out,
+                         uint64_t* part_states_host, uint64_t* exchanged_host);
+
+/* The exchange of the last chunk of the last run: counts_host[s * n + o]
+ * successors from partition s owned by o, seg_off_host[s * n + o] the inbox
+ * offset of that segment, in_begin_host[o] (n + 1 entries) the start of owner
+ * o's inbox.  Synchronous. */
+ht_status part_reach_last_exchange(part_reach_t* c, uint32_t* counts_host, uint32_t* seg_off_host,
+                                   uint32_t* in_begin_host);
+
 /* reach(model, init) for callers that cannot allocate device memory -- code
  * that must not call cudaMalloc (and so cannot create a context), e.g. a
  * process whose device memory is fixed at start-up.  There is no counterpart

@@ -40,6 +40,8 @@ EXPORTED = [
     "ht_bytes_n", "ht_create_n_at", "ht_buckets_for_bytes", "vss_line_divide",
     "reach_ctx_bytes_n", "reach_ctx_create_n_at", "reach_ctx_buckets_for_bytes",
     "reach_ctx_run_times", "vss_probe_random_cfg",
+    "part_reach_bytes", "part_reach_create_at", "part_reach_destroy", "part_reach_run",
+    "part_reach_last_exchange",
 ]
 
 
@@ -126,6 +128,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "reach_ctx_level_ns": [_VP, _VP, _VP, ctypes.c_uint32, ctypes.POINTER(ctypes.c_uint32)],
         "vss_probe_random": [_VP, _u64, _u64, _i, _VP, ctypes.POINTER(ctypes.c_float)],
         "vss_probe_random_cfg": [_VP, _u64, _u64, _i, _i, _i, _i, _VP, ctypes.POINTER(ctypes.c_float)],
+        "part_reach_bytes": [_i, _i, _i, _u64, ctypes.POINTER(_u64)],
+        "part_reach_create_at": [_i, _i, _i, _u64, ctypes.POINTER(ht_params), _VP, _u64,
+                                 ctypes.POINTER(_VP)],
+        "part_reach_destroy": [_VP],
+        "part_reach_run": [_VP, ctypes.POINTER(reach_model), _VP, _VP, _VP, ctypes.c_uint32,
+                           ctypes.POINTER(reach_result), _VP, ctypes.POINTER(_u64)],
+        "part_reach_last_exchange": [_VP, _VP, _VP, _VP],
         "vss_gen_keys": [_u64, _u64, _u64, _u64, _VP, _i, _VP, _VP],
         "ht_find_or_put_stream": [_VP, _u64, _u64, _u64, _u64, _VP, _VP, _VP],
         "reach_batch_bytes": [_VP, _VP, _i, ctypes.c_uint32, _u64, ctypes.POINTER(_u64)],
@@ -701,6 +710,75 @@ class ReachContext:
 
     def scan(self):
         return ht_scan(self.table_handle(), current_stream())
+
+
+# ---------------------------------------------------------------------------
+# Owner-partitioned reachability (static partitioning, K owners on one GPU).
+# ---------------------------------------------------------------------------
+
+def part_reach_bytes(n_parts: int, log2_buckets_part: int, max_state_words: int,
+                     exchange_rows: int) -> int:
+    out = _u64()
+    _check(load().part_reach_bytes(n_parts, log2_buckets_part, max_state_words, exchange_rows,
+                                   ctypes.byref(out)), "part_reach_bytes")
+    return out.value
+
+
+class PartReach:
+    """n_parts owner partitions of 2^log2_buckets_part buckets each on one
+    GPU (part_reach_*), device memory from a torch tensor."""
+
+    def __init__(self, n_parts: int, log2_buckets_part: int, max_state_words: int,
+                 exchange_rows: int = 1 << 20, max_levels: int = 1 << 14, device="cuda", **params):
+        torch = _torch()
+        self.n_parts, self.max_levels = n_parts, max_levels
+        self.params = make_params(**params)
+        nbytes = part_reach_bytes(n_parts, log2_buckets_part, max_state_words, exchange_rows)
+        self.mem = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        aligned = (self.mem.data_ptr() + 255) // 256 * 256
+        h = _VP()
+        _check(load().part_reach_create_at(n_parts, log2_buckets_part, max_state_words, exchange_rows,
+                                           ctypes.byref(self.params), aligned, nbytes, ctypes.byref(h)),
+               "part_reach_create_at")
+        self.handle = h.value
+
+    def close(self):
+        if self.handle:
+            load().part_reach_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, model, raise_on_error: bool = True):
+        """(ReachOutput, states per partition, successors exchanged between partitions)."""
+        a = _ModelArgs(model)
+        levels = np.zeros(self.max_levels, dtype=np.uint64)
+        parts = np.zeros(self.n_parts, dtype=np.uint64)
+        ex = _u64()
+        r = reach_result()
+        st = load().part_reach_run(self.handle, ctypes.byref(a.struct), a.init.ctypes.data,
+                                   current_stream(), levels.ctypes.data, self.max_levels,
+                                   ctypes.byref(r), parts.ctypes.data, ctypes.byref(ex))
+        if raise_on_error:
+            _check(st, "part_reach_run")
+        lv = [int(x) for x in levels[:min(r.n_levels, self.max_levels)]]
+        out = ReachOutput(int(r.states), int(r.transitions), int(r.deadlocks), int(r.digest), lv,
+                          int(r.busy_waits), int(r.rehashes), int(st))
+        return out, [int(x) for x in parts], int(ex.value)
+
+    def last_exchange(self):
+        """(counts [n, n], inbox segment offsets [n, n], inbox starts [n + 1]) of the last chunk."""
+        K = self.n_parts
+        counts = np.zeros((K, K), dtype=np.uint32)
+        seg = np.zeros((K, K), dtype=np.uint32)
+        begin = np.zeros(K + 1, dtype=np.uint32)
+        _check(load().part_reach_last_exchange(self.handle, counts.ctypes.data, seg.ctypes.data,
+                                               begin.ctypes.data), "part_reach_last_exchange")
+        return counts, seg, begin
 
 
 # ---------------------------------------------------------------------------

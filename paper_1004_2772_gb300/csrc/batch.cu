@@ -19,7 +19,10 @@
 // Claim word: epoch (14 bits) | phase (2 bits) | units (24 bits) | claimed (24 bits).
 // A warp that adds to `claimed` and finds it below `units` owns those units of
 // that epoch; the epoch cannot advance until they are reported done, so the
-// per-epoch fields it reads (double-buffered by epoch parity) stay valid.
+// per-epoch fields it reads (double-buffered by epoch parity) stay valid.  An
+// EXPAND unit is a group of grp[epoch & 1] frontier rows: one row while the
+// level has at most kExpandUnitsMax rows, more for larger levels, so that a
+// level of any size fits the 24-bit fields.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -208,6 +211,14 @@ __device__ void publish(BatchModel& M, uint32_t epoch, uint32_t phase, uint32_t 
   atomicExch(&M.claim, pack_claim(epoch, phase, units, 0));
 }
 
+// An EXPAND epoch over `rows` frontier rows: groups of rows as units when the
+// level has more rows than kExpandUnitsMax.
+__device__ void publish_expand(BatchModel& M, uint32_t epoch, uint32_t rows) {
+  const uint32_t g = rows <= kExpandUnitsMax ? 1u : (rows + kExpandUnitsMax - 1) / kExpandUnitsMax;
+  M.grp[epoch & 1u] = g;
+  publish(M, epoch, PH_EXPAND, (rows + g - 1) / g);
+}
+
 // Set up the next epoch of model M after epoch e (phase ph) completed.  Run by
 // one thread, the one that reported the epoch's last unit.
 template <int L>
@@ -242,7 +253,7 @@ __device__ void advance(BatchModel& M, const BatchGlobal& g, uint32_t e, uint32_
       M.n_levels = 1;
       atomicAdd(&M.digest, (unsigned long long)fingerprint(v, M.W));
       atomicAdd(&M.ctr.stored, 1ull);
-      publish(M, e1, PH_EXPAND, 1);
+      publish_expand(M, e1, 1);
     } else {
       // a grown table is clear: re-insert the old one and copy the frontier
       const uint32_t nrb = (uint32_t)(((1ull << ldm(M.log2_nb)) + kRehashUnit - 1) / kRehashUnit);
@@ -258,7 +269,7 @@ __device__ void advance(BatchModel& M, const BatchGlobal& g, uint32_t e, uint32_
     M.fr[0] = ldm(M.nfr[0]);
     M.fr[1] = ldm(M.nfr[1]);
     M.log2_nb = ldm(M.nlog2);
-    publish(M, e1, PH_EXPAND, ldm(M.n_cur));
+    publish_expand(M, e1, ldm(M.n_cur));
     return;
   }
   // PH_EXPAND done
@@ -323,7 +334,7 @@ __device__ void advance(BatchModel& M, const BatchGlobal& g, uint32_t e, uint32_
       return;
     }
   }
-  publish(M, e1, PH_EXPAND, n_next);
+  publish_expand(M, e1, n_next);
 }
 
 template <int L>
@@ -402,12 +413,15 @@ __global__ void __launch_bounds__(256, 2) k_reach_batch(BatchGlobal g) {
       if (cl_phase(w) == PH_EXPAND) {
         // the model's fair share of the grid: its level spread over
         // warps / active models, so that a lone model's level takes one short
-        // round on every warp while many models keep claims large
+        // round on every warp while many models keep claims large (in units
+        // of grp rows: at most one round of spw_max rows when grp is 1)
         const uint32_t warps = gridDim.x * (blockDim.x >> 5);
         uint32_t active = g.mb ? ld_relaxed(&g.st->active) : g.n_models - ld_relaxed(&g.st->finished);
         active = active < 1u ? 1u : active;
+        const uint32_t gr = ldm(M.grp[cl_epoch(w) & 1u]);
+        const uint32_t cap = gr >= M.spw_max ? 1u : M.spw_max / (gr ? gr : 1u);
         take = (uint32_t)(((uint64_t)cl_units(w) * active + warps - 1) / warps);
-        take = take < 1u ? 1u : (take > M.spw_max ? M.spw_max : take);
+        take = take < 1u ? 1u : (take > cap ? cap : take);
       }
       const unsigned long long old = atom_add_acqrel64(&M.claim, take);
       e = cl_epoch(old);
@@ -439,9 +453,15 @@ __global__ void __launch_bounds__(256, 2) k_reach_batch(BatchGlobal g) {
       const SModel sm = model_view(M.blob);
       Acc acc;
       LocalCounters lc;
-      expand_round<kBatchNV, L, true>(t, sm, ldm(M.fr[cur]), ldm(M.n_cur), u0, cnt,
-                                      ldm(M.fr[cur ^ 1u]), &M.next_count[e & 1u],
-                                      (uint32_t)(1ull << lg), acc, lc, wsm);
+      // the claimed units' rows, in rounds of at most spw_max rows
+      const uint32_t n_cur = ldm(M.n_cur), gr = ldm(M.grp[e & 1u]);
+      const uint64_t lo = (uint64_t)u0 * gr;
+      const uint64_t hi = min((uint64_t)(u0 + cnt) * gr, (uint64_t)n_cur);
+      for (uint64_t b = lo; b < hi; b += M.spw_max) {
+        const uint32_t spw = (uint32_t)min((uint64_t)M.spw_max, hi - b);
+        expand_round<kBatchNV, L, true>(t, sm, ldm(M.fr[cur]), n_cur, b, spw, ldm(M.fr[cur ^ 1u]),
+                                        &M.next_count[e & 1u], (uint32_t)(1ull << lg), acc, lc, wsm);
+      }
       const unsigned long long tr = warp_sum((unsigned long long)acc.transitions);
       const unsigned long long dl = warp_sum((unsigned long long)acc.deadlocks);
       const unsigned long long dg = warp_sum(acc.digest);
@@ -478,8 +498,9 @@ __global__ void __launch_bounds__(256, 2) k_reach_batch(BatchGlobal g) {
             if (r != FOP_NEW && r != FOP_ERR) latch_error(&M.ctr, HT_ERR_INVALID);  // a duplicate
           }
         } else {
-          const uint64_t row = (uint64_t)(u - nrb) * kCopyUnit + lane;
-          if (row < n_cur) {
+          for (uint32_t i = lane; i < kCopyUnit; i += 32) {
+            const uint64_t row = (uint64_t)(u - nrb) * kCopyUnit + i;
+            if (row >= n_cur) break;
             Vec<kBatchNV> v;
             load_row_cg_rt<kBatchNV>(ofr + row * M.nv, v, M.nv);
             store_row_rt<kBatchNV>(nfr + row * M.nv, v, M.nv);

@@ -9,9 +9,14 @@ enum : uint32_t { PH_CLEAR = 0, PH_EXPAND = 1, PH_REHASH = 2, PH_DONE = 3 };
 
 constexpr uint32_t kClearUnit = 8192;   // buckets zeroed per unit (256 per lane)
 constexpr uint32_t kRehashUnit = 1024;  // old buckets re-inserted per unit (32 per lane)
-constexpr uint32_t kCopyUnit = 32;      // frontier rows copied per unit (one per lane)
+constexpr uint32_t kCopyUnit = 1024;    // frontier rows copied per unit (32 per lane)
 constexpr int kBatchNV = 8;             // state vectors up to 32 words
-constexpr uint32_t kUnitsMax = (1u << 24) - 1;
+constexpr uint32_t kUnitsMax = (1u << 24) - 1;  // the claim word's unit and claimed fields
+// Units of an EXPAND epoch stay at or below 2^23: warps that race past the end
+// of an epoch add their claim to the claimed field anyway, and the headroom up
+// to kUnitsMax keeps those additions from carrying into the units field.  A
+// level of more frontier rows counts groups of rows as units (BatchModel::grp).
+constexpr uint32_t kExpandUnitsMax = 1u << 23;
 
 struct __align__(16) BatchModel {
   const int* blob;                  // packed model (global memory)
@@ -30,6 +35,7 @@ struct __align__(16) BatchModel {
   unsigned long long claim;         // see the file comment
   uint32_t done[2];
   uint32_t next_count[2];
+  uint32_t grp[2];                  // EXPAND epochs: frontier rows per unit, by epoch parity
   uint32_t n_cur;                   // rows of fr[cur]
   uint32_t level;                   // index of the level in fr[cur]
   uint32_t n_rehash_b;              // REHASH units below this are bucket units
