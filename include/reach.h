@@ -90,7 +90,12 @@ typedef struct {
                              shuffles and writes / compares the row in 16-byte chunks
                              (line_buckets must be 0 or 4*group_lanes, dedup 0).  The
                              reach_*, batch and serving entry points accept only 1 */
-  uint32_t reserved;      /* must be 0 */
+  uint32_t rehash;        /* line sequence after the first line (Alg. "find-or-put": rehash with
+                             the next hash function): 0 (default) = double hashing, the
+                             line advances by an odd step taken from the memo (a step in
+                             [1, lines - 1] for tables of any size); 1 = the next line
+                             (linear probing over lines).  The batch and serving entry
+                             points accept only 0 */
   uint64_t hash_seed;     /* seed of the table hash; default a fixed constant */
 } ht_params;
 

@@ -55,7 +55,7 @@ class ht_params(ctypes.Structure):
     _fields_ = [("line_buckets", ctypes.c_uint32), ("max_rehash", ctypes.c_uint32),
                 ("max_spin", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("dedup", ctypes.c_uint32), ("bucket_bits", ctypes.c_uint32),
-                ("group_lanes", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("group_lanes", ctypes.c_uint32), ("rehash", ctypes.c_uint32),
                 ("hash_seed", ctypes.c_uint64)]
 
 

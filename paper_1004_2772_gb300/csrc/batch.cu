@@ -92,6 +92,7 @@ __device__ __forceinline__ TableView model_table(const BatchModel& M, const Batc
   t.nv = M.nv;
   t.bucket_bits = 32;
   t.lines = lines;
+  t.rehash_linear = 0;
   t.lines_div = DivU64{0, 0, 0};  // power-of-two tables only
   return t;
 }
@@ -611,8 +612,8 @@ ht_status reach_batch_create_at(const reach_model* models, const int32_t* const*
   ht_params p{};
   st = resolve_params(params, 1u << 10, &p);
   if (st != HT_OK) return st;
-  // batch tables use 32-bit buckets walked by one thread per key
-  if (p.bucket_bits != 32 || p.group_lanes != 1) return HT_ERR_INVALID;
+  // batch tables use 32-bit buckets walked by one thread per key, double hashing
+  if (p.bucket_bits != 32 || p.group_lanes != 1 || p.rehash != 0) return HT_ERR_INVALID;
   reach_batch_t* b = new (std::nothrow) reach_batch_t();
   if (!b) return HT_ERR_OOM;
   b->n_models = n_models;

@@ -40,6 +40,7 @@ struct TableView {
   uint32_t nv;            // ceil(W / 4)
   uint32_t bucket_bits;   // 32 or 16: width of a bucket word
   uint32_t lines;         // nb / line_buckets
+  uint32_t rehash_linear; // 1: the next line after a full line; 0: double hashing
   DivU64 lines_div;       // division by `lines`; m == 0 marks a power-of-two table
 };
 

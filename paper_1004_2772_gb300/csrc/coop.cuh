@@ -51,6 +51,7 @@ __device__ __forceinline__ int find_or_put_group(const TableView& t, const Vec<N
     line = div_r(t.lines_div, h >> kLog2L);
     step = 1u + __umulhi(memo << 1, t.lines - 1u);
   }
+  if (t.rehash_linear) step = 1u;  // ht_params.rehash = 1: the next line
   // masks in walk order: bit p <-> bucket (off + p) mod L
   auto rot = [&](uint32_t m) -> uint32_t {
     return off ? ((m >> off) | (m << (L - off))) & kAll : m;

@@ -316,8 +316,8 @@ ht_status serve_open_at(void* mem_dev, uint64_t mem_bytes, uint32_t n_slots, uin
   ht_params p{};
   ht_status st = resolve_params(params, 1u << 10, &p);
   if (st != HT_OK) return st;
-  // batch tables use 32-bit buckets walked by one thread per key
-  if (p.bucket_bits != 32 || p.group_lanes != 1) return HT_ERR_INVALID;
+  // batch tables use 32-bit buckets walked by one thread per key, double hashing
+  if (p.bucket_bits != 32 || p.group_lanes != 1 || p.rehash != 0) return HT_ERR_INVALID;
   serve_t* s = new (std::nothrow) serve_t();
   if (!s) return HT_ERR_OOM;
   s->n_slots = n_slots;

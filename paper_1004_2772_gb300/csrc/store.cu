@@ -255,7 +255,7 @@ ht_status resolve_params(const ht_params* in, uint64_t nb, ht_params* out) {
   if (in) p = *in;
   if (p.bucket_bits == 0) p.bucket_bits = 32;
   if (p.group_lanes == 0) p.group_lanes = 1;
-  if (p.reserved != 0) return HT_ERR_INVALID;
+  if (p.rehash > 1) return HT_ERR_INVALID;
   if (p.group_lanes != 1) {
     // a group of G lanes reads a line of 4G 32-bit buckets at once
     const uint32_t G = p.group_lanes;
@@ -313,6 +313,7 @@ ht_status table_init_at(ht_t* h, uint64_t nb, int max_words, const ht_params* pa
   h->view.state_words = (uint32_t)max_words;
   h->view.nv = (uint32_t)nv;
   h->view.bucket_bits = h->params.bucket_bits;
+  h->view.rehash_linear = h->params.rehash;
   h->nb = nb;
   h->max_words = max_words;
   h->bytes = mem_bytes;

@@ -23,7 +23,8 @@
 // a bucket can undergo is empty -> write(memo) -> done(memo), so a stale
 // non-empty word is still correct and a stale empty word is corrected by the
 // CAS.  After the line: next line = (line + (2*memo + 1)) mod lines (double
-// hashing with an odd step over a power-of-two line count, Section 3.2).
+// hashing with an odd step over a power-of-two line count, Section 3.2), or
+// line + 1 when the table's rehash rule is the next line.
 #pragma once
 
 #include "common.cuh"
@@ -208,6 +209,7 @@ __device__ __forceinline__ int find_or_put(const TableView& t, const Vec<NV>& ke
     constexpr int kMemoBits = BW == 32 ? 31 : 15;
     step = 1u + __umulhi(memo << (32 - kMemoBits), t.lines - 1u);
   }
+  if (t.rehash_linear) step = 1u;  // ht_params.rehash = 1: the next line
 
   for (uint32_t r = 0; r <= t.max_rehash; ++r) {
     if (r) {
