@@ -305,6 +305,11 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="hashtable: tune parameters first")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--models", type=int, default=256, help="batch: number of models")
+    ap.add_argument("--probe-gib", type=float, default=16.0, help="probe-sweep: buffer size (GiB)")
+    ap.add_argument("--probe-modes", default="0,1,2,3,4,5,6,7,8", help="probe-sweep: modes")
+    ap.add_argument("--probe-default-shape", action="store_true",
+                    help="probe-sweep: only the default shape (8 in flight, 8 blocks/SM, 256 threads)")
+    ap.add_argument("--probe-reps", type=int, default=3, help="probe-sweep: timed runs per shape")
     args = ap.parse_args()
     global LOG2_BUCKETS
     LOG2_BUCKETS = args.log2_buckets or WORKLOADS[args.workload][1]
@@ -863,14 +868,17 @@ def run_probe_sweep(args, world, rank, local, dev):
     buffer: the plateau of each mode is the roofline denominator bench.py
     uses.  value = the plateau of 32-byte sector reads."""
     from paper_1004_2772_gb300 import binding
+    modes = tuple(int(x) for x in args.probe_modes.split(","))
+    shapes = {m: [(8, 8, 256)] for m in modes} if args.probe_default_shape else None
     with ClockSampler(local) as clocks:
-        rows = binding.probe_sweep(gib=16, n_access=1 << 28, modes=tuple(range(9)))
-    best = {m: max((r for r in rows if r["mode"] == m), key=lambda r: r["per_s"]) for m in range(9)}
+        rows = binding.probe_sweep(gib=args.probe_gib, n_access=1 << 28, modes=modes,
+                                   reps=args.probe_reps, shapes=shapes)
+    best = {m: max((r for r in rows if r["mode"] == m), key=lambda r: r["per_s"]) for m in modes}
     line = base_line(args, world, "random 32-byte sector reads/sec on 1 GB300 (probe plateau)",
-                     best[0]["per_s"], "accesses/s", None,
-                     {"workload": "random-access-probe-16GiB", "accesses_per_run": 1 << 28,
-                      "l2": "16 GiB buffer, larger than L2"})
-    line["plateau"] = {binding.PROBE_MODES[m]: best[m] for m in range(9)}
+                     best[modes[0]]["per_s"], "accesses/s", None,
+                     {"workload": f"random-access-probe-{args.probe_gib:g}GiB", "accesses_per_run": 1 << 28,
+                      "modes": list(modes), "l2": f"{args.probe_gib:g} GiB buffer, larger than L2"})
+    line["plateau"] = {binding.PROBE_MODES[m]: best[m] for m in modes}
     line["rows"] = rows
     line["clocks"] = clocks.summary()
     if rank == 0:

@@ -69,7 +69,13 @@ def served():
 
 
 def _server(cuda_lib):
+    import gc
+
     import torch
+    # the previous server's arena goes back to the driver first: the budget is
+    # a share of what the device has free
+    gc.collect()
+    torch.cuda.empty_cache()
     free, _ = torch.cuda.mem_get_info()
     return cuda_lib.Server(budget_bytes=int(free * 0.85), n_slots=64, max_levels=4096)
 
@@ -84,6 +90,7 @@ def test_served_stream_full_size_all_queued(cuda_lib, served):
     for jid, (_, m), e in zip(ids, jobs, want):
         _same(got[jid].result, e, m.name)
     srv.close()
+    del srv
 
 
 def test_served_stream_full_size_real_time(cuda_lib, served):
@@ -103,3 +110,4 @@ def test_served_stream_full_size_real_time(cuda_lib, served):
         _same(got[jid].result, e, m.name)
     assert srv.status()["kernel_launches"] >= 1
     srv.close()
+    del srv
