@@ -733,8 +733,12 @@ def serve_stats(jobs, slots_list, plain, local):
     server of each slot count (HBM budget = 85% of free memory): aggregate
     states/s, p50/p99 latency; with `plain`, each job alone through reach()
     in arrival order (device time of each run, host overheads excluded)."""
+    import gc
+
     import torch
     from paper_1004_2772_gb300 import binding
+    gc.collect()
+    torch.cuda.empty_cache()  # earlier measurements' memory back to the driver before sizing
     free, _ = torch.cuda.mem_get_info()
     out = {}
     with ClockSampler(local) as clocks:
