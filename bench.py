@@ -331,7 +331,7 @@ def main():
 
     # random-access rates of this GPU (the random-sector roofline's denominators):
     # each mode's plateau over the probe shapes
-    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
+    rates = binding.random_access_rates(gib=args.probe_gib, n_access=1 << 28)
     model = workload_model(args.workload)
     mode = {"persistent": binding.REACH_PERSISTENT, "per-level": binding.REACH_PER_LEVEL,
             "graph": binding.REACH_GRAPH}[args.mode]
