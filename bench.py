@@ -55,35 +55,57 @@ WORKLOADS = {
 LOG2_BUCKETS = 26
 MAX_LEVELS = 1 << 14
 # DRAM traffic of a kernel (dram__bytes_read.sum + dram__bytes_write.sum, ncu,
-# one launch of a small case of the workload) per unit of work, with the hash
-# of the kernel sources the capture ran: kernel -> {"unit": ..., "bytes_per_unit":
-# ..., "sources_sha": ..., "capture": ...}.  A line reports it (scaled to the
-# run's units) only while the sources still hash the same; otherwise traffic is
-# null and the line says why.
-RECORDED_TRAFFIC: dict = {}
+# one launch) per unit of work, recorded with the hash of the CUDA sources the
+# kernel is compiled from (KERNEL_SOURCES).  A line reports it, scaled to the
+# run's units, only while those sources still hash the same and only for the
+# workload it was captured on (traffic per unit depends on how much of the table
+# L2 holds, so it does not carry over to other sizes); otherwise traffic is null
+# and traffic_source says why.  Key: "kernel:workload".
+RECORDED_TRAFFIC: dict = {
+    "k_reach_persistent:beem-medium": {
+        "unit": "transition", "bytes_per_unit": 2060577024 / 21937569,
+        "sources_sha": "ddac276d9d641ee5",
+        "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum, "
+                   "one launch of the BEEM-shaped medium model (seed 7: 5,478,076 states, 21,937,569 "
+                   "transitions, 2^24 buckets): 1.297 GB read + 0.763 GB written"},
+}
+
+# the CUDA sources (paper_1004_2772_gb300/csrc) each measured kernel is compiled from
+KERNEL_SOURCES = {
+    "k_reach_persistent": ["common.cuh", "divide.h", "table.cuh", "expand.cuh", "reach_kernels.cuh",
+                           "reach.cu", "reach_k16.cu", "reach_k32_lo.cu", "reach_k32_hi.cu"],
+    "k_find_or_put_stream": ["common.cuh", "divide.h", "table.cuh", "coop.cuh", "stream.cu"],
+    "k_find_or_put": ["common.cuh", "divide.h", "table.cuh", "coop.cuh", "store.cu"],
+    "k_reach_batch": ["common.cuh", "divide.h", "table.cuh", "expand.cuh", "batch.h", "batch.cu"],
+}
 
 
-def kernel_sources_sha() -> str:
-    """sha256 (first 16 hex digits) of the CUDA sources and the C-ABI header."""
-    import glob
+def kernel_sources_sha(kernel: str) -> str:
+    """sha256 (first 16 hex digits) of the CUDA sources of `kernel`."""
     import hashlib
-    pkg = os.path.join(ROOT, "paper_1004_2772_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(pkg, "*.cu")) + glob.glob(os.path.join(pkg, "*.cuh"))
-                   + glob.glob(os.path.join(pkg, "*.h"))) + [os.path.join(ROOT, "include", "reach.h")]
+    csrc = os.path.join(ROOT, "paper_1004_2772_gb300", "csrc")
     h = hashlib.sha256()
-    for f in files:
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for f in KERNEL_SOURCES.get(kernel, []):
+        h.update(f.encode())
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, units: float):
+def recorded_traffic(key: str, units: float):
     """(traffic bytes for `units` units of work or None, a note on its source)."""
-    rec = RECORDED_TRAFFIC.get(kernel)
-    sha = kernel_sources_sha()
+    kernel = key.split(":")[0]
+    sha = kernel_sources_sha(kernel)
+    rec = RECORDED_TRAFFIC.get(key)
     if rec is None:
-        return None, {"kernel_sources_sha": sha, "note": "no DRAM capture recorded for this kernel"}
+        note = {"kernel_sources_sha": sha,
+                "note": "no DRAM capture recorded for this kernel on this workload"}
+        other = {k: v for k, v in RECORDED_TRAFFIC.items() if k.split(":")[0] == kernel}
+        if other:  # the same kernel captured on a smaller workload, for reference
+            note["smaller_workload_captures"] = {k: {"bytes_per_unit": v["bytes_per_unit"], "unit": v["unit"],
+                                                     "current": v["sources_sha"] == sha}
+                                                 for k, v in other.items()}
+        return None, note
     if rec["sources_sha"] != sha:
         return None, {"kernel_sources_sha": sha, "capture_sources_sha": rec["sources_sha"],
                       "note": "the kernel sources changed since the DRAM capture"}
@@ -306,7 +328,7 @@ def main():
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--models", type=int, default=256, help="batch: number of models")
     ap.add_argument("--probe-gib", type=float, default=16.0, help="probe-sweep: buffer size (GiB)")
-    ap.add_argument("--probe-modes", default="0,1,2,3,4,5,6,7,8", help="probe-sweep: modes")
+    ap.add_argument("--probe-modes", default="0,1,2,3,4,5,6,7,8,9,10", help="probe-sweep: modes")
     ap.add_argument("--probe-default-shape", action="store_true",
                     help="probe-sweep: only the default shape (8 in flight, 8 blocks/SM, 256 threads)")
     ap.add_argument("--probe-reps", type=int, default=3, help="probe-sweep: timed runs per shape")

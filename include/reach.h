@@ -564,6 +564,9 @@ ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_access, int
  * that number) run in waves.  One more mode:
  *   8  read 4 bytes of a random 32-byte sector (DRAM still moves the sector
  *      into L2; 4 bytes go back to the SM: the memory side of mode 0)
+ *   9  read a random 64-byte unit by two lanes, 32 bytes each, in one load
+ *      instruction (n_access counts units; every lane keeps `inflight`)
+ *  10  read a random 128-byte line by four lanes in one instruction
  * HT_ERR_INVALID for a shape or mode outside these.  Synchronous. */
 ht_status vss_probe_random_cfg(void* buf_dev, uint64_t bytes, uint64_t n_access, int mode,
                                int inflight, int blocks_per_sm, int threads, void* stream,

@@ -32,20 +32,35 @@ __device__ __forceinline__ uint64_t probe_unit(uint64_t seed, uint64_t a, uint64
 // gpu-scope store of one 32- / 16-bit word (the claim and publish steps of an
 // insert, for either bucket width); 8: read 4 bytes of a random 32 B sector
 // (the whole sector still comes from DRAM into L2, only 4 bytes go back to
-// the SM: the memory side of mode 0 without its return traffic).
+// the SM: the memory side of mode 0 without its return traffic); 9: read 64 B
+// by two lanes, 32 B each, in one load instruction; 10: read a 128 B line by
+// four lanes in one instruction.  In modes 9 and 10 an access is the group's:
+// n_access counts groups, and every lane of a group keeps INF of them in flight.
 // INF accesses per thread are issued before any is consumed.
 template <int MODE, int INF>
 __global__ void __launch_bounds__(256, 1) k_probe(uint4* buf, uint64_t n_units, uint64_t n_access,
                                                 uint64_t seed, unsigned long long* sink) {
-  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+  // lanes per access: one, or a pair / quad of adjacent lanes reading one unit together
+  constexpr int G = MODE == 9 ? 2 : MODE == 10 ? 4 : 1;
+  const uint64_t tid = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x / G;
+  const uint32_t part = threadIdx.x & (G - 1);  // this lane's 32 bytes of the unit
   uint32_t acc = 0;
   uint64_t base = tid * INF;
   for (; base < n_access; base += nthr * INF) {
     uint64_t u[INF];
 #pragma unroll
     for (int k = 0; k < INF; ++k) u[k] = probe_unit(seed, base + k, n_units);
-    if (MODE == 0 || MODE == 1 || MODE == 8) {
+    if (MODE == 9 || MODE == 10) {
+      if (base + INF > n_access) break;  // a partial group: the tail loop below
+      uint4 v[INF][2];
+#pragma unroll
+      for (int k = 0; k < INF; ++k) ld_cg_v8(buf + u[k] * (2 * G) + 2 * part, v[k][0], v[k][1]);
+#pragma unroll
+      for (int k = 0; k < INF; ++k)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) acc ^= v[k][q].x ^ v[k][q].y ^ v[k][q].z ^ v[k][q].w;
+    } else if (MODE == 0 || MODE == 1 || MODE == 8) {
       if (base + INF > n_access) break;  // a partial group: the tail loop below
       // whole groups are unpredicated and every word read is used, so each
       // read keeps its own registers until all INF are issued
@@ -102,10 +117,14 @@ __global__ void __launch_bounds__(256, 1) k_probe(uint4* buf, uint64_t n_units, 
     }
   }
   // reads of the last partial group (at most INF - 1 per thread), one at a time
-  if (MODE == 0 || MODE == 1 || MODE == 8) {
+  if (MODE == 0 || MODE == 1 || MODE == 8 || MODE == 9 || MODE == 10) {
     for (uint64_t a = base; a < n_access && a < base + INF; ++a) {
       const uint64_t u = probe_unit(seed, a, n_units);
-      if (MODE == 8) {
+      if (MODE == 9 || MODE == 10) {
+        uint4 x, y;
+        ld_cg_v8(buf + u * (2 * G) + 2 * part, x, y);
+        acc ^= x.x ^ x.y ^ x.z ^ x.w ^ y.x ^ y.y ^ y.z ^ y.w;
+      } else if (MODE == 8) {
         acc ^= __ldcg(reinterpret_cast<const unsigned int*>(buf + u * 2));
       } else {
         constexpr int C = MODE == 1 ? 4 : 2;
@@ -133,7 +152,7 @@ using ProbeKernel = void (*)(uint4*, uint64_t, uint64_t, uint64_t, unsigned long
 // the registers a shape needs.
 template <int MODE>
 static ProbeKernel probe_kernel_inf(int inf) {
-  constexpr int kMaxInf = MODE == 1 ? 8 : MODE == 0 ? 16 : 64;
+  constexpr int kMaxInf = MODE == 1 ? 8 : (MODE == 0 || MODE >= 9) ? 16 : 64;
   switch (inf) {
     case 1: return k_probe<MODE, 1>;
     case 2: return k_probe<MODE, 2>;
@@ -157,6 +176,8 @@ static ProbeKernel probe_kernel(int mode, int inf) {
     case 6: return probe_kernel_inf<6>(inf);
     case 7: return probe_kernel_inf<7>(inf);
     case 8: return probe_kernel_inf<8>(inf);
+    case 9: return probe_kernel_inf<9>(inf);
+    case 10: return probe_kernel_inf<10>(inf);
     default: return nullptr;
   }
 }
@@ -171,14 +192,14 @@ extern "C" ht_status vss_probe_random_cfg(void* buf_dev, uint64_t bytes, uint64_
   if (inflight == 0) inflight = 8;
   if (blocks_per_sm == 0) blocks_per_sm = 8;
   if (threads == 0) threads = 256;
-  if (!buf_dev || !ms || mode < 0 || mode > 8 || (reinterpret_cast<uintptr_t>(buf_dev) & 255u))
+  if (!buf_dev || !ms || mode < 0 || mode > 10 || (reinterpret_cast<uintptr_t>(buf_dev) & 255u))
     return HT_ERR_INVALID;
   if (blocks_per_sm < 1 || blocks_per_sm > 64 || threads < 32 || threads > 1024 || (threads & 31))
     return HT_ERR_INVALID;
   const ProbeKernel kern = probe_kernel(mode, inflight);
   if (!kern) return HT_ERR_INVALID;
   if (threads > 256) return HT_ERR_INVALID;  // the kernels' launch bound
-  const uint64_t unit = (mode == 1) ? 64 : 32;
+  const uint64_t unit = mode == 1 || mode == 9 ? 64 : mode == 10 ? 128 : 32;
   const uint64_t n_units = bytes / unit;
   if (n_units < 1024 || n_access == 0) return HT_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -92,3 +92,20 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "states/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_recorded_traffic_only_for_the_same_kernel_sources(monkeypatch):
+    sha = bench.kernel_sources_sha("k_reach_persistent")
+    assert len(sha) == 16 and sha != bench.kernel_sources_sha("k_reach_batch")
+    rec = {"unit": "transition", "bytes_per_unit": 100.0, "sources_sha": sha, "capture": "x"}
+    monkeypatch.setattr(bench, "RECORDED_TRAFFIC", {"k_reach_persistent:w": rec})
+    t, src = bench.recorded_traffic("k_reach_persistent:w", 10)
+    assert t == 1000.0 and src["bytes_per_unit"] == 100.0
+    # another workload of the same kernel: null, with the capture shown for reference
+    t, src = bench.recorded_traffic("k_reach_persistent:other", 10)
+    assert t is None and "k_reach_persistent:w" in src["smaller_workload_captures"]
+    # sources changed since the capture: null
+    monkeypatch.setattr(bench, "RECORDED_TRAFFIC",
+                        {"k_reach_persistent:w": dict(rec, sources_sha="0" * 16)})
+    t, src = bench.recorded_traffic("k_reach_persistent:w", 10)
+    assert t is None and "changed" in src["note"]
