@@ -51,6 +51,7 @@ WORKLOADS = {
     "batch": (None, 0),
     "serve": (None, 0),
     "probe-sweep": (None, 0),
+    "part": (dict(seed=22, update_pct=40), 26),
 }
 LOG2_BUCKETS = 26
 MAX_LEVELS = 1 << 14
@@ -332,6 +333,7 @@ def main():
     ap.add_argument("--probe-default-shape", action="store_true",
                     help="probe-sweep: only the default shape (8 in flight, 8 blocks/SM, 256 threads)")
     ap.add_argument("--probe-reps", type=int, default=3, help="probe-sweep: timed runs per shape")
+    ap.add_argument("--parts", type=int, default=4, help="part: owner partitions")
     args = ap.parse_args()
     global LOG2_BUCKETS
     LOG2_BUCKETS = args.log2_buckets or WORKLOADS[args.workload][1]
@@ -346,9 +348,10 @@ def main():
     dev = torch.device("cuda", local)
     _build.build()
     binding.load()
-    if args.workload in ("hashtable", "hashtable-sweep", "batch", "serve", "probe-sweep"):
+    if args.workload in ("hashtable", "hashtable-sweep", "batch", "serve", "probe-sweep", "part"):
         {"hashtable": run_hashtable, "hashtable-sweep": run_hashtable_sweep, "batch": run_batch,
-         "serve": run_serve, "probe-sweep": run_probe_sweep}[args.workload](args, world, rank, local, dev)
+         "serve": run_serve, "probe-sweep": run_probe_sweep,
+         "part": run_part}[args.workload](args, world, rank, local, dev)
         return
 
     # random-access rates of this GPU (the random-sector roofline's denominators):
@@ -906,6 +909,55 @@ def run_probe_sweep(args, world, rank, local, dev):
                       "modes": list(modes), "l2": f"{args.probe_gib:g} GiB buffer, larger than L2"})
     line["plateau"] = {binding.PROBE_MODES[m]: best[m] for m in modes}
     line["rows"] = rows
+    line["clocks"] = clocks.summary()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_part(args, world, rank, local, dev):
+    """The BEEM-shaped workload on K owner partitions of one GPU (static
+    partitioning: successors exchanged between owners every level) against
+    the shared table (the paper's comparison of the two architectures).
+    value = states/s of the partitioned run (host-driven levels; wall time of
+    part_reach_run, which synchronises once per level)."""
+    import torch
+    from paper_1004_2772_gb300 import binding
+    model = workload_model("part")
+    K = args.parts
+    lg = LOG2_BUCKETS - (K.bit_length() - 1)
+    pr = binding.PartReach(K, lg, model.state_words)
+    for _ in range(max(1, args.warmup)):
+        ref, parts, ex = pr.run(model)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            got, parts, ex = pr.run(model)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    assert (got.states, got.digest, got.level_sizes) == (ref.states, ref.digest, ref.level_sizes)
+    pr.close()
+    del pr
+    torch.cuda.empty_cache()
+    ctx = binding.ReachContext(LOG2_BUCKETS, model.state_words, max_levels=MAX_LEVELS)
+    ctx.load(model)
+    for _ in range(3):
+        ctx.run(binding.REACH_PERSISTENT)
+    shared = ctx.result()
+    for _ in range(args.steps):
+        ctx.run(binding.REACH_PERSISTENT)
+    shared_ms = float(np.mean(ctx.run_times(min(args.steps, 64))))
+    ctx.close()
+    assert (shared.states, shared.digest) == (got.states, got.digest)
+    line = base_line(args, world, f"states/sec on 1 GB300 (owner-partitioned reachability, {K} owners)",
+                     got.states / (ms / 1e3), "states/s", ms,
+                     {"workload": model.name, "parts": K, "log2_buckets_per_part": lg,
+                      "states": got.states, "transitions": got.transitions,
+                      "l2": "inputs larger than L2 (tables and frontiers, GBs)"})
+    line["exchanged"] = ex
+    line["exchanged_frac"] = ex / got.transitions
+    line["part_states"] = parts
+    line["shared_table"] = {"ms_per_run": shared_ms, "states_per_s": shared.states / (shared_ms / 1e3)}
     line["clocks"] = clocks.summary()
     if rank == 0:
         print(json.dumps(line), flush=True)
