@@ -80,6 +80,20 @@ def test_guarded_model_row_shapes(cuda_lib, W):
         check(cuda_lib, ctx, m, mode, ref)
 
 
+@pytest.mark.parametrize("P,W", [(16, 16), (24, 24), (31, 32)])
+def test_rounds_with_more_successors_than_descriptors(cuda_lib, P, W):
+    """Every state has 2P successors (32, 48 or 62), so 32 states have more
+    of them than the warp's 960 descriptors: a round holds only
+    960 / (2P) states (the per-lane descriptor slices of the worst-case
+    fan-out).  All three drivers, and tracing."""
+    m = synth.interleaving_model(11, [2] * P, W) if P <= 16 else \
+        synth.interleaving_model(11, [2] * 12 + [1] * (P - 12), W)
+    ref = oracle.reach(m)
+    ctx = cuda_lib.ReachContext(log2_for(ref.states), W, max_levels=4096)
+    for mode in MODES + [cuda_lib.REACH_PERSISTENT | cuda_lib.REACH_TRACE]:
+        check(cuda_lib, ctx, m, mode, ref)
+
+
 def test_repeated_runs_and_reload(cuda_lib):
     ctx = cuda_lib.ReachContext(18, 16, max_levels=4096)
     a = synth.tiny_interleaving_model()
