@@ -334,6 +334,8 @@ def main():
                     help="probe-sweep: only the default shape (8 in flight, 8 blocks/SM, 256 threads)")
     ap.add_argument("--probe-reps", type=int, default=3, help="probe-sweep: timed runs per shape")
     ap.add_argument("--parts", type=int, default=4, help="part: owner partitions")
+    ap.add_argument("--exchange-rows", type=int, default=1 << 23,
+                    help="part: rows of one exchange chunk (outbox and inbox each)")
     args = ap.parse_args()
     global LOG2_BUCKETS
     LOG2_BUCKETS = args.log2_buckets or WORKLOADS[args.workload][1]
@@ -925,7 +927,7 @@ def run_part(args, world, rank, local, dev):
     model = workload_model("part")
     K = args.parts
     lg = LOG2_BUCKETS - (K.bit_length() - 1)
-    pr = binding.PartReach(K, lg, model.state_words)
+    pr = binding.PartReach(K, lg, model.state_words, exchange_rows=args.exchange_rows)
     for _ in range(max(1, args.warmup)):
         ref, parts, ex = pr.run(model)
     torch.cuda.synchronize()
@@ -952,6 +954,7 @@ def run_part(args, world, rank, local, dev):
     line = base_line(args, world, f"states/sec on 1 GB300 (owner-partitioned reachability, {K} owners)",
                      got.states / (ms / 1e3), "states/s", ms,
                      {"workload": model.name, "parts": K, "log2_buckets_per_part": lg,
+                      "exchange_rows": args.exchange_rows,
                       "states": got.states, "transitions": got.transitions,
                       "l2": "inputs larger than L2 (tables and frontiers, GBs)"})
     line["exchanged"] = ex
