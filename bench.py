@@ -576,7 +576,7 @@ def run_hashtable(args, world, rank, local, dev):
     if args.autotune:
         tuned = autotune.tune_table(LOG2_BUCKETS, args.load_factor, args.dist, cache_path=None)
         params = dict(tuned["best"])
-    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
+    rates = binding.random_access_rates(gib=args.probe_gib, n_access=1 << 28)
     r = hashtable_point(LOG2_BUCKETS, args.load_factor, args.dist, args.key_mode, params, args.steps,
                         args.warmup, rates, local)
     t_max = max_over_ranks(r["ms_per_fill"], world, dev)
@@ -611,7 +611,7 @@ def run_hashtable_sweep(args, world, rank, local, dev):
     fills repeated).  value = calls/s at 2^26, LF 0.75, uniform, fused."""
     import torch
     from paper_1004_2772_gb300 import binding, synth
-    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
+    rates = binding.random_access_rates(gib=args.probe_gib, n_access=1 << 28)
     min_calls = int(float(os.environ.get("BENCH_SWEEP_MIN_CALLS", "1e9")))
     points = []
     t_all = time.perf_counter()
@@ -740,7 +740,7 @@ def run_batch(args, world, rank, local, dev):
     launch."""
     from paper_1004_2772_gb300 import binding
     models = synth.batched_models(count=args.models, first_seed=1)
-    rates = binding.random_access_rates(gib=16, n_access=1 << 28)
+    rates = binding.random_access_rates(gib=args.probe_gib, n_access=1 << 28)
     r = batch_stats(models, args.steps, args.warmup, rates, local)
     t_max = max_over_ranks(r["ms_per_batch"], world, dev)
     value = sum_over_ranks(float(r["states"]), world, dev) / (t_max / 1e3)
