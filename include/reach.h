@@ -232,7 +232,7 @@ ht_status ht_find_or_put_stream(ht_t* h, uint64_t seed, uint64_t n_ids, uint64_t
  * firing it sets v[p] = edge_dst[e] and, when upd_var[e] >= 0,
  * v[P + upd_var[e]] = upd_val[e].  Every enabled edge is one transition.
  * Limits (HT_ERR_INVALID otherwise): the sum over processes of the largest
- * out-degree of a local state is at most 960 (the successors of one state
+ * out-degree of a local state is at most 1920 (the successors of one state
  * must fit one warp's round), and the packed model (about P + sum(n_local)
  * + 5E words) fits 128 KiB. */
 typedef struct {
@@ -567,6 +567,14 @@ ht_status vss_probe_random(void* buf_dev, uint64_t bytes, uint64_t n_access, int
  *   9  read a random 64-byte unit by two lanes, 32 bytes each, in one load
  *      instruction (n_access counts units; every lane keeps `inflight`)
  *  10  read a random 128-byte line by four lanes in one instruction
+ *  11  read a random 64-byte unit by one thread with one bulk asynchronous
+ *      copy (cp.async.bulk) into its slot in shared memory, completion
+ *      counted on the thread's own mbarrier (inflight 1, 2, 4 or 8)
+ *  12  write a random 64-byte unit by one thread with one bulk asynchronous
+ *      copy from its slot in shared memory (inflight 1, 2, 4 or 8)
+ * Modes 11 and 12 use threads * inflight * 64 + threads * 8 bytes of shared
+ * memory per block; their mbarrier waits are bounded and a wait that runs
+ * out returns HT_ERR_TIMEOUT.
  * HT_ERR_INVALID for a shape or mode outside these.  Synchronous. */
 ht_status vss_probe_random_cfg(void* buf_dev, uint64_t bytes, uint64_t n_access, int mode,
                                int inflight, int blocks_per_sm, int threads, void* stream,

@@ -414,7 +414,8 @@ def vss_probe_random_cfg(buf_dev: int, nbytes: int, n_access: int, mode: int, in
 
 PROBE_MODES = {0: "read 32 B", 1: "read 64 B", 2: "write 32 B", 3: "atomic 32-bit",
                4: "CAS 32-bit", 5: "CAS 16-bit", 6: "store 32-bit", 7: "store 16-bit",
-               8: "read 4 B of a 32 B sector", 9: "read 64 B by 2 lanes", 10: "read 128 B by 4 lanes"}
+               8: "read 4 B of a 32 B sector", 9: "read 64 B by 2 lanes", 10: "read 128 B by 4 lanes",
+               11: "read 64 B by one bulk copy", 12: "write 64 B by one bulk copy"}
 
 # Probe shapes swept for each mode: (accesses in flight per thread, blocks per
 # SM, threads per block).  Reads hold their data in registers, so their
@@ -424,6 +425,8 @@ PROBE_SHAPES = {
     0: [(i, b, t) for i in (2, 4, 8, 16) for b in (8, 32) for t in (128, 256)],
     1: [(i, b, t) for i in (2, 4, 8) for b in (8, 32) for t in (128, 256)],
     8: [(i, b, t) for i in (4, 8, 16, 32, 64) for b in (8, 32) for t in (128, 256)],
+    11: [(i, b, t) for i in (1, 2, 4, 8) for b in (8, 32) for t in (128, 256)],
+    12: [(i, b, t) for i in (1, 2, 4, 8) for b in (8, 32) for t in (128, 256)],
 }
 DEFAULT_WRITE_SHAPES = [(i, b, 256) for i in (4, 8, 16) for b in (8, 32)]
 

@@ -7,9 +7,13 @@
 namespace vss {
 
 #ifndef VSS_DESC_CAP
-#define VSS_DESC_CAP 960  // with 16-word rows, four blocks of 8 warps fit in shared memory
+#define VSS_DESC_CAP 960  // words per warp: with 16-word rows, four blocks of 8 warps fit in shared memory
 #endif
-constexpr int kDescCap = VSS_DESC_CAP;  // successor descriptors per warp and round
+// A successor descriptor is the 16-bit index of its edge in the device model
+// (a model blob of at most 2^15 words holds fewer than 2^16 edges; the edge
+// carries its process), so a warp's descriptor words hold two per word.
+using desc_t = uint16_t;
+constexpr int kDescCap = 2 * VSS_DESC_CAP;  // successor descriptors per warp and round
 
 #ifndef VSS_WARP_DEDUP
 #define VSS_WARP_DEDUP 0  // merge equal successors of one warp iteration before probing
@@ -18,7 +22,7 @@ constexpr int kDescCap = VSS_DESC_CAP;  // successor descriptors per warp and ro
 template <int NV>
 __host__ __device__ constexpr int row_stride() { return 4 * NV + 4; }  // padded: conflict-free 16 B reads
 
-__host__ __device__ constexpr int warp_smem_words_nv(int nv) { return 32 * (4 * nv + 4) + kDescCap + 32; }
+__host__ __device__ constexpr int warp_smem_words_nv(int nv) { return 32 * (4 * nv + 4) + VSS_DESC_CAP + 32; }
 
 struct SModel {
   int P, S, W, crit_any, maxfan, spw_max;
@@ -28,6 +32,12 @@ struct SModel {
   const int4* edges;
   const int* uval;
 };
+
+// An edge of the device model: x = destination local state (bits 0-15) and
+// its process (bits 16-30), y / z = guard variable / value, w = updated
+// variable (-1 = none).
+__device__ __forceinline__ int edge_dst(const int4& E) { return E.x & 0xFFFF; }
+__device__ __forceinline__ int edge_proc(const int4& E) { return E.x >> 16; }
 
 // Per-thread counters (a thread sees far fewer than 2^32 transitions between
 // flushes); the digest needs all 64 bits.
@@ -64,7 +74,7 @@ __device__ __forceinline__ void vec_set(Vec<NV>& v, int i, uint32_t x) {
 // Phase 1 of a round, warp-cooperatively: the warp takes frontier rows
 // [base, base + spw) (spw <= 32); lane i < spw reads state i's row, keeps it
 // (and its hash sum) in shared memory, and lists the enabled edges of the
-// state (next-state) as descriptors (edge | process << 24) in its own slice of
+// state (next-state) as descriptors (16-bit edge indices) in its own slice of
 // the warp's descriptor area; it counts the state's transitions and, when
 // there are none, a deadlock.  A warp scan of the counts gives the round's T
 // successors (returned; the inclusive prefix per lane stays in shared memory).
@@ -77,8 +87,8 @@ __device__ __forceinline__ uint32_t round_successors(const TableView& t, const S
                                                      const TraceDev* tr) {
   constexpr int RS = row_stride<NV>();
   uint32_t* rows = wsm;
-  uint32_t* desc = wsm + 32 * RS;
-  uint32_t* pref = desc + kDescCap;
+  desc_t* desc = reinterpret_cast<desc_t*>(wsm + 32 * RS);
+  uint32_t* pref = wsm + 32 * RS + VSS_DESC_CAP;
   const unsigned lane = lane_id();
   const int P = m.P;
   const int maxfan = m.maxfan;
@@ -104,7 +114,7 @@ __device__ __forceinline__ uint32_t round_successors(const TableView& t, const S
         ncrit += (cp >= 0 && rw[p] == cp) ? 1 : 0;
       }
     }
-    uint32_t* d = desc + lane * maxfan;
+    desc_t* d = desc + lane * maxfan;
     for (int p = 0; p < P; ++p) {
       const int s = rw[p];
       const int b = m.base[p] + s;
@@ -113,9 +123,9 @@ __device__ __forceinline__ uint32_t round_successors(const TableView& t, const S
       const int e_end = m.eb[b + 1];
       for (int e = m.eb[b]; e < e_end; ++e) {
         const int4 E = m.edges[e];
-        if (E.y >= 0 && rw[P + E.y] != E.z) continue;      // guard
-        if (cp >= 0 && E.x == cp && others > 0) continue;  // mutex
-        d[c++] = (uint32_t)e | ((uint32_t)p << 24);
+        if (E.y >= 0 && rw[P + E.y] != E.z) continue;                  // guard
+        if (cp >= 0 && edge_dst(E) == cp && others > 0) continue;     // mutex
+        d[c++] = (desc_t)e;
       }
     }
     acc.transitions += c;
@@ -152,25 +162,25 @@ __device__ __forceinline__ void round_successor(const TableView& t, const SModel
                                                 uint64_t& h, uint32_t& parent_idx) {
   constexpr int RS = row_stride<NV>();
   const uint32_t* rows = wsm;
-  const uint32_t* desc = wsm + 32 * RS;
-  const uint32_t* pref = desc + kDescCap;
+  const desc_t* desc = reinterpret_cast<const desc_t*>(wsm + 32 * RS);
+  const uint32_t* pref = wsm + 32 * RS + VSS_DESC_CAP;
   const int P = m.P;
   uint32_t o = 0;  // owner = first lane whose inclusive prefix exceeds j
 #pragma unroll
   for (uint32_t step = 16; step > 0; step >>= 1)
     if (pref[o + step - 1] <= j) o += step;
   const uint32_t k = j - (o ? pref[o - 1] : 0u);
-  const uint32_t dd = desc[o * m.maxfan + k];
-  const int e = (int)(dd & 0xFFFFFFu);
-  const int p = (int)(dd >> 24);
+  const int e = (int)desc[o * m.maxfan + k];
   const int4 E = m.edges[e];
+  const int p = edge_proc(E);
   const uint32_t* ro = rows + o * RS;
   const uint4* r = reinterpret_cast<const uint4*>(ro);
 #pragma unroll
   for (int q = 0; q < NV; ++q) w.c[q] = r[q];
   uint64_t hs = (uint64_t)ro[4 * NV] | ((uint64_t)ro[4 * NV + 1] << 32);
-  hs += hash_term(t.seed, p, (uint32_t)E.x) - hash_term(t.seed, p, ro[p]);
-  vec_set(w, p, (uint32_t)E.x);
+  const uint32_t dst = (uint32_t)edge_dst(E);
+  hs += hash_term(t.seed, p, dst) - hash_term(t.seed, p, ro[p]);
+  vec_set(w, p, dst);
   if (E.w >= 0) {
     const int q = P + E.w;
     const uint32_t uv = (uint32_t)m.uval[e];

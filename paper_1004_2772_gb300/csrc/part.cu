@@ -307,7 +307,7 @@ struct part_reach {
 static bool part_shape_ok(int n_parts, int log2_buckets_part, int max_state_words, uint64_t exchange_rows) {
   return n_parts >= 1 && n_parts <= kMaxParts && (n_parts & (n_parts - 1)) == 0 && log2_buckets_part >= 10 &&
          log2_buckets_part <= 31 && max_state_words >= 1 && max_state_words <= 32 &&
-         exchange_rows >= (uint64_t)kDescCap && exchange_rows <= (1ull << 31);
+         exchange_rows >= (uint64_t)VSS_DESC_CAP && exchange_rows <= (1ull << 31);
 }
 
 static uint64_t part_bytes(int K, int log2p, int words, uint64_t cap) {
@@ -413,7 +413,9 @@ ht_status part_reach_run(part_reach_t* c, const reach_model* m, const int32_t* i
   const size_t smem = (size_t)((smem_words + 3) & ~3) * 4 + (size_t)8 * warp_smem_words_nv(ks.nv) * 4;
   if (smem > 200 * 1024) return HT_ERR_INVALID;
   const uint32_t maxfan = (uint32_t)std::max(1, blob[13]);
-  const uint32_t spw = (uint32_t)blob[14];
+  // a warp round's successors (spw states of at most maxfan each) fit one outbox chunk
+  if (maxfan > c->cap) return HT_ERR_INVALID;
+  const uint32_t spw = (uint32_t)std::min<uint64_t>((uint64_t)blob[14], c->cap / maxfan);
   VSS_CUDA_TRY(cudaMemcpyAsync(c->blob, blob.data(), blob.size() * 4, cudaMemcpyHostToDevice, s));
   for (int k = 0; k < c->K; ++k) {
     st = table_clear(&c->tables[k], s);
@@ -447,8 +449,8 @@ ht_status part_reach_run(part_reach_t* c, const reach_model* m, const int32_t* i
   pd.next = c->fr[1 - cur];
   ks.seed<<<1, 1, 0, s>>>(pd);
   VSS_CUDA_TRY(cudaGetLastError());
-  // rounds per chunk: the chunk's successors (at most kDescCap per round) fit the outbox
-  const uint32_t rpc = (uint32_t)std::max<uint64_t>(1, c->cap / std::min<uint64_t>(kDescCap, (uint64_t)spw * maxfan));
+  // rounds per chunk: the chunk's successors (at most spw * maxfan per round) fit the outbox
+  const uint32_t rpc = (uint32_t)std::max<uint64_t>(1, c->cap / ((uint64_t)spw * maxfan));
   std::vector<uint64_t> levels;
   const size_t zero_off = offsetof(PartTotals, out_count);
   const size_t zero_len = offsetof(PartTotals, seg_off) - zero_off;

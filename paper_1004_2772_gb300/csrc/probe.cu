@@ -139,7 +139,121 @@ __global__ void __launch_bounds__(256, 1) k_probe(uint4* buf, uint64_t n_units, 
   if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);  // keeps the loads alive
 }
 
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (the copy engine of each SM, cp.async.bulk) of one
+// 64-byte unit per access, issued by one thread:
+// mode 11: global -> the thread's slot in shared memory, completion counted
+//          in bytes on the thread's own mbarrier;
+// mode 12: the thread's slot in shared memory -> global, completion by bulk
+//          group.
+// Every wait on an mbarrier is bounded: after kBulkWaitPolls polls the kernel
+// records a timeout in err and waits once more, again bounded, for its copies.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kBulkWaitPolls = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kBulkWaitPolls; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src),
+               "r"(bytes)
+               : "memory");
+}
+
+template <int MODE, int INF>
+__global__ void __launch_bounds__(256, 1) k_probe_bulk(uint4* buf, uint64_t n_units, uint64_t n_access,
+                                                     uint64_t seed, unsigned long long* sink) {
+  extern __shared__ __align__(128) unsigned char bulk_sm[];
+  uint4* slot = reinterpret_cast<uint4*>(bulk_sm) + (size_t)threadIdx.x * INF * 4;  // INF x 64 B
+  uint64_t* bars = reinterpret_cast<uint64_t*>(bulk_sm + (size_t)blockDim.x * INF * 64);
+  const uint32_t bar = smem_u32(bars + threadIdx.x);
+  unsigned long long* err = sink + 1;
+  if (MODE == 11) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  } else {
+    // the slots' contents are stored from shared memory: fill them once
+    for (int k = 0; k < INF * 4; ++k) slot[k] = make_uint4(threadIdx.x, k, 0u, 0u);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthr = (uint64_t)gridDim.x * blockDim.x;
+  uint32_t acc = 0, parity = 0;
+  bool failed = false;
+  for (uint64_t base = tid * INF; base < n_access && !failed; base += nthr * INF) {
+    const int cnt = (int)(n_access - base < (uint64_t)INF ? n_access - base : (uint64_t)INF);
+    uint64_t u[INF];
+#pragma unroll
+    for (int k = 0; k < INF; ++k) u[k] = probe_unit(seed, base + k, n_units);
+    if (MODE == 11) {
+      mbar_expect_tx(bar, 64u * (uint32_t)cnt);
+#pragma unroll
+      for (int k = 0; k < INF; ++k)
+        if (k < cnt) bulk_g2s(smem_u32(slot + 4 * k), buf + u[k] * 4, 64u, bar);
+      if (!mbar_wait_bounded(bar, parity)) {
+        atomicExch(err, 1ull);
+        failed = true;
+        mbar_wait_bounded(bar, parity);  // let the copies in flight land before leaving
+        break;
+      }
+      parity ^= 1u;
+#pragma unroll
+      for (int k = 0; k < INF; ++k)
+        if (k < cnt)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc ^= slot[4 * k + q].x ^ slot[4 * k + q].w;
+    } else {
+#pragma unroll
+      for (int k = 0; k < INF; ++k)
+        if (k < cnt) bulk_s2g(buf + u[k] * 4, smem_u32(slot + 4 * k), 64u);
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    }
+  }
+  if (MODE == 12) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  if (acc == 0x9E3779B9u) atomicAdd(sink, 1ull);  // keeps the copies' data alive
+}
+
 using ProbeKernel = void (*)(uint4*, uint64_t, uint64_t, uint64_t, unsigned long long*);
+
+template <int MODE>
+static ProbeKernel probe_bulk_kernel(int inf) {
+  switch (inf) {
+    case 1: return k_probe_bulk<MODE, 1>;
+    case 2: return k_probe_bulk<MODE, 2>;
+    case 4: return k_probe_bulk<MODE, 4>;
+    case 8: return k_probe_bulk<MODE, 8>;
+    default: return nullptr;
+  }
+}
 
 // Accesses in flight per thread that each mode is compiled for: reads keep
 // their data in registers until all INF have been issued (8 registers per
@@ -178,6 +292,8 @@ static ProbeKernel probe_kernel(int mode, int inf) {
     case 8: return probe_kernel_inf<8>(inf);
     case 9: return probe_kernel_inf<9>(inf);
     case 10: return probe_kernel_inf<10>(inf);
+    case 11: return probe_bulk_kernel<11>(inf);
+    case 12: return probe_bulk_kernel<12>(inf);
     default: return nullptr;
   }
 }
@@ -192,14 +308,15 @@ extern "C" ht_status vss_probe_random_cfg(void* buf_dev, uint64_t bytes, uint64_
   if (inflight == 0) inflight = 8;
   if (blocks_per_sm == 0) blocks_per_sm = 8;
   if (threads == 0) threads = 256;
-  if (!buf_dev || !ms || mode < 0 || mode > 10 || (reinterpret_cast<uintptr_t>(buf_dev) & 255u))
+  if (!buf_dev || !ms || mode < 0 || mode > 12 || (reinterpret_cast<uintptr_t>(buf_dev) & 255u))
     return HT_ERR_INVALID;
   if (blocks_per_sm < 1 || blocks_per_sm > 64 || threads < 32 || threads > 1024 || (threads & 31))
     return HT_ERR_INVALID;
   const ProbeKernel kern = probe_kernel(mode, inflight);
   if (!kern) return HT_ERR_INVALID;
   if (threads > 256) return HT_ERR_INVALID;  // the kernels' launch bound
-  const uint64_t unit = mode == 1 || mode == 9 ? 64 : mode == 10 ? 128 : 32;
+  const bool bulk = mode == 11 || mode == 12;
+  const uint64_t unit = mode == 1 || mode == 9 || bulk ? 64 : mode == 10 ? 128 : 32;
   const uint64_t n_units = bytes / unit;
   if (n_units < 1024 || n_access == 0) return HT_ERR_INVALID;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -209,19 +326,31 @@ extern "C" ht_status vss_probe_random_cfg(void* buf_dev, uint64_t bytes, uint64_
   // the sink word lives in the first 8 bytes of the buffer's last unit (probe data is garbage)
   unsigned long long* sink =
       reinterpret_cast<unsigned long long*>(static_cast<char*>(buf_dev) + (n_units - 1) * unit);
+  // bulk modes: each thread's INF 64-byte slots and its 8-byte mbarrier in shared memory
+  const size_t smem = bulk ? (size_t)threads * inflight * 64 + (size_t)threads * 8 : 0;
+  if (bulk) {
+    VSS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // sink word and the bulk kernels' timeout word
+    VSS_CUDA_TRY(cudaMemsetAsync(sink, 0, 16, s));
+  }
   cudaEvent_t e0, e1;
   VSS_CUDA_TRY(cudaEventCreate(&e0));
   VSS_CUDA_TRY(cudaEventCreate(&e1));
   uint4* b = static_cast<uint4*>(buf_dev);
   const uint64_t n_use = n_units - 1;  // keep the sink unit out of the random range
   VSS_CUDA_TRY(cudaEventRecord(e0, s));
-  kern<<<sms * blocks_per_sm, threads, 0, s>>>(b, n_use, n_access, 0x1234567ull, sink);
+  kern<<<sms * blocks_per_sm, threads, smem, s>>>(b, n_use, n_access, 0x1234567ull, sink);
   VSS_CUDA_TRY(cudaGetLastError());
   VSS_CUDA_TRY(cudaEventRecord(e1, s));
   VSS_CUDA_TRY(cudaEventSynchronize(e1));
   VSS_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (bulk) {
+    unsigned long long timed_out = 0;
+    VSS_CUDA_TRY(cudaMemcpy(&timed_out, sink + 1, 8, cudaMemcpyDeviceToHost));
+    if (timed_out) return HT_ERR_TIMEOUT;
+  }
   return HT_OK;
 }
 

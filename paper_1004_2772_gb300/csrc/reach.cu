@@ -89,6 +89,10 @@ static uint64_t ctx_bytes(uint64_t nb, int max_words, uint32_t max_levels) {
 }
 
 namespace vss {
+// successor descriptors are 16-bit edge indices: a full blob (5 words per
+// edge) holds fewer than 2^16 edges
+static_assert(kModelMaxWords / 5 < (1 << 16), "edge index must fit a 16-bit descriptor");
+
 ht_status pack_model(const reach_model* m, const int32_t* init, int max_words,
                      std::vector<int>& blob) {
   if (!m || !init) return HT_ERR_INVALID;
@@ -155,8 +159,15 @@ ht_status pack_model(const reach_model* m, const int32_t* init, int max_words,
     blob[off_crit + p] = m->crit[p];
   }
   for (long long i = 0; i <= nl_total; ++i) blob[off_eb + i] = m->edge_begin[i];
+  {
+    // each edge carries its process above its destination (edge_dst / edge_proc)
+    long long b = 0;
+    for (int p = 0; p < P; ++p)
+      for (int s = 0; s < m->n_local[p]; ++s, ++b)
+        for (int e = m->edge_begin[b]; e < m->edge_begin[b + 1]; ++e)
+          blob[off_edges + 4LL * e + 0] = m->edge_dst[e] | (p << 16);
+  }
   for (int e = 0; e < E; ++e) {
-    blob[off_edges + 4LL * e + 0] = m->edge_dst[e];
     blob[off_edges + 4LL * e + 1] = m->guard_var[e];
     blob[off_edges + 4LL * e + 2] = m->guard_val[e];
     blob[off_edges + 4LL * e + 3] = m->upd_var[e];

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 def test_every_swept_shape_runs(cuda_lib):
     b = cuda_lib
-    modes = tuple(range(11))
+    modes = tuple(range(13))
     rows = b.probe_sweep(gib=0.5, n_access=1 << 22, modes=modes, reps=1)
     want = sum(len(b.PROBE_SHAPES.get(m, b.DEFAULT_WRITE_SHAPES)) for m in modes)
     assert len(rows) == want
@@ -27,8 +27,8 @@ def test_unsupported_shapes_are_refused(cuda_lib):
     ptr = (buf.data_ptr() + 255) // 256 * 256
     n = (64 << 20) - 256
     for mode, inf, bps, thr in ((0, 32, 8, 256), (1, 16, 8, 256), (8, 128, 8, 256), (0, 8, 8, 512),
-                                (0, 8, 65, 256), (0, 3, 8, 256), (11, 8, 8, 256), (0, 8, 8, 48),
-                                (9, 32, 8, 256)):
+                                (0, 8, 65, 256), (0, 3, 8, 256), (13, 8, 8, 256), (0, 8, 8, 48),
+                                (9, 32, 8, 256), (11, 16, 8, 256), (12, 32, 8, 256)):
         with pytest.raises(b.HtError):
             b.vss_probe_random_cfg(ptr, n, 1 << 16, mode, inf, bps, thr)
     # the default shape still answers through both entry points

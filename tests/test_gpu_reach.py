@@ -82,16 +82,58 @@ def test_guarded_model_row_shapes(cuda_lib, W):
 
 @pytest.mark.parametrize("P,W", [(16, 16), (24, 24), (31, 32)])
 def test_rounds_with_more_successors_than_descriptors(cuda_lib, P, W):
-    """Every state has 2P successors (32, 48 or 62), so 32 states have more
-    of them than the warp's 960 descriptors: a round holds only
-    960 / (2P) states (the per-lane descriptor slices of the worst-case
-    fan-out).  All three drivers, and tracing."""
+    """Every state has 2P successors (32, 48 or 62); a round holds
+    min(32, 1920 / (2P)) states (the per-lane descriptor slices of the
+    worst-case fan-out in the warp's 1920 descriptors): 32, 32 and 30.
+    All three drivers, and tracing."""
     m = synth.interleaving_model(11, [2] * P, W) if P <= 16 else \
         synth.interleaving_model(11, [2] * 12 + [1] * (P - 12), W)
     ref = oracle.reach(m)
     ctx = cuda_lib.ReachContext(log2_for(ref.states), W, max_levels=4096)
     for mode in MODES + [cuda_lib.REACH_PERSISTENT | cuda_lib.REACH_TRACE]:
         check(cuda_lib, ctx, m, mode, ref)
+
+
+def _fan_model(k):
+    """Six 4-state interleaving processes (4096 states, 12 successors each)
+    and a seventh process with one local state and k parallel self-loops:
+    every state has 12 + k successors, k of them itself."""
+    base = synth.interleaving_model(5, [4] * 6, 8)
+    edges = []
+    for p in range(6):
+        b0 = int(base.edge_begin[4 * p])
+        ep = []
+        for s in range(4):
+            lo, hi = int(base.edge_begin[4 * p + s]), int(base.edge_begin[4 * p + s + 1])
+            ep.append([(int(base.edge_dst[e]), -1, 0, -1, 0) for e in range(lo, hi)])
+        assert b0 == 8 * p
+        edges.append(ep)
+    edges.append([[(0, -1, 0, -1, 0)] * k])
+    return synth.build_model(f"fan-{12 + k}", [4] * 6 + [1], edges, 8)
+
+
+@pytest.mark.parametrize("k", [100, 1000, 1908])
+def test_rounds_of_few_states(cuda_lib, k):
+    """Fan-outs of 112, 1012 and 1920 successors per state: a warp round
+    holds 17, 1 and 1 states, and the last fills all 1920 descriptors."""
+    m = _fan_model(k)
+    ref = oracle.reach(m)
+    assert (ref.states, ref.transitions) == (4096, 4096 * (12 + k))
+    ctx = cuda_lib.ReachContext(14, 8, max_levels=4096)
+    for mode in MODES:
+        check(cuda_lib, ctx, m, mode, ref)
+
+
+def test_fan_out_beyond_the_descriptor_area_is_refused(cuda_lib):
+    """1921 successors per state do not fit one warp round: the model is
+    refused before any launch."""
+    ctx = cuda_lib.ReachContext(14, 8, max_levels=4096)
+    with pytest.raises(cuda_lib.HtError) as e:
+        ctx.load(_fan_model(1909))
+    assert e.value.status == cuda_lib.HT_ERR_INVALID
+    # the context still runs a model that fits
+    m = _fan_model(100)
+    check(cuda_lib, ctx, m, 0, oracle.reach(m))
 
 
 def test_repeated_runs_and_reload(cuda_lib):
