@@ -64,11 +64,11 @@ MAX_LEVELS = 1 << 14
 # and traffic_source says why.  Key: "kernel:workload".
 RECORDED_TRAFFIC: dict = {
     "k_reach_persistent:beem-medium": {
-        "unit": "transition", "bytes_per_unit": 2060577024 / 21937569,
-        "sources_sha": "ddac276d9d641ee5",
+        "unit": "transition", "bytes_per_unit": (1313702656 + 766255616) / 21937569,
+        "sources_sha": "d65aa8695b0bdb44",
         "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum, "
                    "one launch of the BEEM-shaped medium model (seed 7: 5,478,076 states, 21,937,569 "
-                   "transitions, 2^24 buckets): 1.297 GB read + 0.763 GB written"},
+                   "transitions, 2^24 buckets): 1.314 GB read + 0.766 GB written"},
     "k_find_or_put_stream:24-0.5-uniform": {
         "unit": "find_or_put", "bytes_per_unit": (1829714176 + 859776768) / 16777216,
         "sources_sha": "23edb5a89cbc1c3c",
@@ -76,11 +76,11 @@ RECORDED_TRAFFIC: dict = {
                    "one fill of a 2^24-bucket table at load 0.5 (16,777,216 calls, 8,388,608 distinct "
                    "16-word keys, uniform): 1.830 GB read + 0.860 GB written"},
     "k_reach_batch:batch64": {
-        "unit": "find_or_put", "bytes_per_unit": (11545390848 + 2136697856) / 122061882,
-        "sources_sha": "d0d5103a4dd4e2db",
+        "unit": "find_or_put", "bytes_per_unit": (11398247168 + 2133536512) / 122061882,
+        "sources_sha": "64b329203dfd9f9a",
         "capture": "ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum, "
                    "one launch of the first 64 models of the batched workload (7,796,054 states, "
-                   "122,061,882 find-or-puts): 11.545 GB read + 2.137 GB written"},
+                   "122,061,882 find-or-puts): 11.398 GB read + 2.134 GB written"},
 }
 
 # the CUDA sources (paper_1004_2772_gb300/csrc) each measured kernel is compiled from
