@@ -368,16 +368,20 @@ def main():
          "part": run_part}[args.workload](args, world, rank, local, dev)
         return
 
-    # random-access rates of this GPU (the random-sector roofline's denominators):
-    # each mode's plateau over the probe shapes
-    rates = binding.random_access_rates(gib=args.probe_gib, n_access=1 << 28)
     model = workload_model(args.workload)
     mode = {"persistent": binding.REACH_PERSISTENT, "per-level": binding.REACH_PER_LEVEL,
             "graph": binding.REACH_GRAPH}[args.mode]
+    # the context is allocated first, as in a process that only runs
+    # reachability: a probe buffer of many GB allocated and freed before it
+    # moves the context elsewhere in device memory, and the kernel's time
+    # with it (by several per cent either way)
     ctx = binding.ReachContext(LOG2_BUCKETS, model.state_words, max_levels=MAX_LEVELS,
                                line_buckets=args.line_buckets)
     ctx.load(model)
     stream = torch.cuda.current_stream()
+    # random-access rates of this GPU (the random-sector roofline's denominators):
+    # each mode's plateau over the probe shapes
+    rates = binding.random_access_rates(gib=args.probe_gib, n_access=1 << 28)
 
     # warm-up (also yields the result that every timed step must reproduce)
     for _ in range(max(3, args.warmup)):
