@@ -200,9 +200,9 @@ static ReachDev make_rd(reach_ctx_t* c) {
 // Blocks per SM for a single-model launch.  On tables of at most 2^20
 // buckets the levels are short and latency-bound: the level barrier, whose
 // cost grows with the number of blocks, weighs more than the memory-level
-// parallelism of a fourth block per SM.
+// parallelism of a third and fourth block per SM.
 #ifndef VSS_SMALL_TABLE_BLOCKS
-#define VSS_SMALL_TABLE_BLOCKS 3
+#define VSS_SMALL_TABLE_BLOCKS 2
 #endif
 static int blocks_per_sm(int occupancy, uint64_t nb) {
   if (VSS_SMALL_TABLE_BLOCKS > 0 && nb <= (1ull << 20) && occupancy > VSS_SMALL_TABLE_BLOCKS)
