@@ -85,11 +85,13 @@ RECORDED_TRAFFIC: dict = {
 
 # the CUDA sources (paper_1004_2772_gb300/csrc) each measured kernel is compiled from
 KERNEL_SOURCES = {
-    "k_reach_persistent": ["common.cuh", "divide.h", "table.cuh", "expand.cuh", "reach_kernels.cuh",
-                           "reach.cu", "reach_k16.cu", "reach_k32_lo.cu", "reach_k32_hi.cu"],
+    "k_reach_persistent": ["common.cuh", "divide.h", "table.cuh", "coop.cuh", "expand.cuh",
+                           "reach_kernels.cuh", "reach.cu", "reach_k16.cu", "reach_k32_lo.cu",
+                           "reach_k32_hi.cu", "reach_group.cu"],
     "k_find_or_put_stream": ["common.cuh", "divide.h", "table.cuh", "coop.cuh", "stream.cu"],
     "k_find_or_put": ["common.cuh", "divide.h", "table.cuh", "coop.cuh", "store.cu"],
-    "k_reach_batch": ["common.cuh", "divide.h", "table.cuh", "expand.cuh", "batch.h", "batch.cu"],
+    "k_reach_batch": ["common.cuh", "divide.h", "table.cuh", "coop.cuh", "expand.cuh", "batch.h",
+                      "batch.cu"],
 }
 
 
@@ -328,6 +330,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="persistent", choices=["persistent", "per-level", "graph"])
     ap.add_argument("--line-buckets", type=int, default=32)
+    ap.add_argument("--group-lanes", type=int, default=1,
+                    help="lanes per successor in the reachability kernel (2, 4, 8: cooperative "
+                         "probing of lines of 4G buckets; the line length follows)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra-configs", action="store_true",
                     help="skip the tiny / hash-table / batch / served measurements of the default line")
@@ -375,8 +380,10 @@ def main():
     # reachability: a probe buffer of many GB allocated and freed before it
     # moves the context elsewhere in device memory, and the kernel's time
     # with it (by several per cent either way)
+    group = {} if args.group_lanes == 1 else {"group_lanes": args.group_lanes}
+    line_buckets = args.line_buckets if args.group_lanes == 1 else 4 * args.group_lanes
     ctx = binding.ReachContext(LOG2_BUCKETS, model.state_words, max_levels=MAX_LEVELS,
-                               line_buckets=args.line_buckets)
+                               line_buckets=line_buckets, **group)
     ctx.load(model)
     stream = torch.cuda.current_stream()
     # random-access rates of this GPU (the random-sector roofline's denominators):
@@ -445,7 +452,9 @@ def main():
     alg = algorithmic_bytes(got.states, got.transitions, model.state_words)
     achieved = alg / (kernel_ms / 1000.0) / 1e9
     kname = {0: "k_reach_persistent", 1: "k_reach_level", 2: "k_reach_step"}[mode]
-    traffic, traffic_src = recorded_traffic(f"{kname}:{args.workload}", got.transitions)
+    traffic, traffic_src = (recorded_traffic(f"{kname}:{args.workload}", got.transitions)
+                            if args.group_lanes == 1 and line_buckets == 32 else
+                            (None, {"note": "DRAM captures are recorded for the default line layout only"}))
     line = {
         "metric": METRIC, "value": value, "unit": "states/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max,
@@ -453,7 +462,8 @@ def main():
         "data": "synthetic",
         "config": {"workload": model.name, "states": got.states, "transitions": got.transitions,
                    "levels": len(got.level_sizes), "state_words": model.state_words,
-                   "log2_buckets": LOG2_BUCKETS, "line_buckets": args.line_buckets,
+                   "log2_buckets": LOG2_BUCKETS, "line_buckets": line_buckets,
+                   "group_lanes": args.group_lanes,
                    "mode": args.mode, "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": l2_note},
         "find_or_put_ops_per_s": trans_all / (t_max / 1000.0),

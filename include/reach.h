@@ -88,8 +88,10 @@ typedef struct {
                              line of 4*group_lanes 32-bit buckets (32, 64 or 128
                              bytes) at once, combines the lanes' bucket masks with
                              shuffles and writes / compares the row in 16-byte chunks
-                             (line_buckets must be 0 or 4*group_lanes, dedup 0).  The
-                             reach_*, batch and serving entry points accept only 1 */
+                             (line_buckets must be 0 or 4*group_lanes, dedup 0).  In
+                             reach_* (not with REACH_TRACE) the G lanes of a group
+                             walk one successor's line together; the batch and
+                             serving entry points accept only 1 */
   uint32_t rehash;        /* line sequence after the first line (Alg. "find-or-put": rehash with
                              the next hash function): 0 (default) = double hashing, the
                              line advances by an odd step taken from the memo (a step in

@@ -44,7 +44,8 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_1004_2772
 
 TABLE_SPACE = {"line_buckets": (8, 16, 32), "bucket_bits": (32, 16), "dedup": (0, 1),
                "group_lanes": (1, 2, 4, 8), "block_threads": (128, 256)}
-REACH_SPACE = {"line_buckets": (8, 16, 32), "bucket_bits": (32, 16), "block_threads": (128, 256)}
+REACH_SPACE = {"line_buckets": (8, 16, 32), "bucket_bits": (32, 16), "group_lanes": (1, 2, 4, 8),
+               "block_threads": (128, 256)}
 # probe sequence, tried on the best layout
 PROBE_SPACE = {"rehash": (0, 1), "max_rehash": (0, 256, 16)}
 REACH_PROBE_SPACE = {"rehash": (0, 1)}

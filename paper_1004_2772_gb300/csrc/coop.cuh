@@ -59,7 +59,7 @@ __device__ __forceinline__ int find_or_put_group(const TableView& t, const Vec<N
 
   for (uint32_t r = 0; r <= t.max_rehash; ++r) {
     if (r) {
-      lc.rehashes++;
+      if (gl == 0) lc.rehashes++;  // once per group
       if ((r & 31) == 0) {  // another key failed: the whole group leaves together
         const bool failed = ld_relaxed(&t.ctr->err) != 0;
         if (__any_sync(gmask, failed)) return FOP_ERR;

@@ -2,6 +2,7 @@
 // single-model drivers (reach.cu) and the batched driver (batch.cu).
 #pragma once
 
+#include "coop.cuh"
 #include "table.cuh"
 
 namespace vss {
@@ -198,18 +199,28 @@ __device__ __forceinline__ void round_successor(const TableView& t, const SModel
 // find-or-put -- so no lane serialises a whole fan-out.  New states are
 // appended to the next frontier (rows) with one atomicAdd per warp and
 // iteration, straight from registers.
-template <int NV, int L, bool RT, bool TR = false, int BW = 32>
+// G > 1 (cooperative probing, coop.cuh): the G lanes of a group build the
+// same successor from shared memory and walk its line of 4G buckets together;
+// an iteration then covers 32 / G successors and the group's first lane
+// answers for it.
+template <int NV, int L, bool RT, bool TR = false, int BW = 32, int G = 1>
 __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m, const uint4* cur,
                                              uint32_t n_cur, uint64_t base, uint32_t spw,
                                              uint4* next, uint32_t* next_count, uint32_t cap,
                                              Acc& acc, LocalCounters& lc, uint32_t* wsm,
                                              const TraceDev* tr = nullptr) {
+  static_assert(G == 1 || ((G == 2 || G == 4 || G == 8) && L == 4 * G && BW == 32 && !RT && !TR &&
+                            !VSS_WARP_DEDUP),
+                "groups of 2, 4 or 8 lanes walk lines of 4G 32-bit buckets");
+  constexpr uint32_t kPer = 32 / G;  // successors per iteration
   const unsigned lane = lane_id();
+  const int gl = (int)(lane & (G - 1));
+  const unsigned gmask = G == 1 ? 0xffffffffu : ((1u << G) - 1u) << (lane & ~(unsigned)(G - 1));
   const uint32_t nvr = RT ? t.nv : (uint32_t)NV;
   const uint32_t T = round_successors<NV, RT, TR>(t, m, cur, n_cur, base, spw, acc, wsm, tr);
-  const uint32_t iters = (T + 31) / 32;
+  const uint32_t iters = (T + kPer - 1) / kPer;
   for (uint32_t it = 0; it < iters; ++it) {
-    const uint32_t j = it * 32 + lane;
+    const uint32_t j = it * kPer + lane / G;  // the same for the lanes of a group
     bool is_new = false;
     uint32_t new_idx = 0;
     Vec<NV> w;
@@ -246,7 +257,14 @@ __device__ __forceinline__ void expand_round(const TableView& t, const SModel& m
 #endif
     int res = FOP_SEEN;
     uint32_t sidx = 0;
-    if (probe) res = find_or_put<NV, L, RT, BW>(t, w, h, sidx, lc);
+    if constexpr (G == 1) {
+      if (probe) res = find_or_put<NV, L, RT, BW>(t, w, h, sidx, lc);
+    } else {
+      if (probe) {  // uniform over the group
+        res = find_or_put_group<NV, G>(t, w, h, sidx, lc, gl, gmask);
+        if (gl != 0) res = FOP_SEEN;  // the group's first lane answers
+      }
+    }
 #if VSS_WARP_DEDUP
     {
       const int lres = __shfl_sync(0xffffffffu, res, lead);

@@ -27,10 +27,13 @@
 
 namespace vss {
 
-static ReachKernels pick_kernels(int nv, int L, int bw) {
+// G > 1: cooperative probing by groups of G lanes (lines of 4G 32-bit buckets).
+static ReachKernels pick_kernels(int nv, int L, int bw, int G = 1) {
   ReachKernels k{};
-  const bool ok = bw == 16 ? reach_kernels_w16(nv, L, &k)
-                           : (reach_kernels_w32_lo(nv, L, &k) || reach_kernels_w32_hi(nv, L, &k));
+  bool ok;
+  if (G > 1) ok = bw == 32 && L == 4 * G && reach_kernels_group(nv, G, &k);
+  else ok = bw == 16 ? reach_kernels_w16(nv, L, &k)
+                     : (reach_kernels_w32_lo(nv, L, &k) || reach_kernels_w32_hi(nv, L, &k));
   return ok ? k : ReachKernels{};
 }
 
@@ -338,7 +341,6 @@ ht_status reach_ctx_create_n_at(uint64_t n_buckets, int max_state_words, uint32_
   if (!c) return HT_ERR_OOM;
   const uint64_t tb = align_up(table_bytes(n_buckets, max_state_words), 256);
   st = table_init_at(&c->table, n_buckets, max_state_words, params, mem_dev, tb);
-  if (st == HT_OK && c->table.params.group_lanes != 1) st = HT_ERR_INVALID;  // one thread per key
   if (st != HT_OK) {
     delete c;
     return st;
@@ -540,7 +542,7 @@ ht_status reach_ctx_run(reach_ctx_t* c, int mode, void* stream) {
   const int threads = (int)c->table.params.block_threads;
   const size_t smem = smem_bytes_for(c, threads);
   const ReachKernels ks = pick_kernels((int)c->table.view.nv, (int)c->table.params.line_buckets,
-                                         (int)c->table.view.bucket_bits);
+                                         (int)c->table.view.bucket_bits, (int)c->table.params.group_lanes);
   if (!ks.persistent) return HT_ERR_INVALID;
   TableView tv = c->table.view;
   ReachDev rd = make_rd(c);
@@ -713,7 +715,6 @@ extern "C" ht_status reach_noalloc(const reach_model* m, const int32_t* init_hos
   const uint64_t tb = align_up(table_bytes(nb, W), 256);
   st = table_init_at(&table, nb, W, params, base, tb);
   if (st != HT_OK) return st;
-  if (table.params.group_lanes != 1) return HT_ERR_INVALID;
   char* p = static_cast<char*>(base) + tb;
   int* blob = reinterpret_cast<int*>(p);
   p += align_up(kModelMaxWords * 4ull, 256);
@@ -750,7 +751,7 @@ extern "C" ht_status reach_noalloc(const reach_model* m, const int32_t* init_hos
   VSS_CUDA_TRY(cudaMemsetAsync(tot, 0, sizeof(ReachTotals), s));
 
   const ReachKernels ks = pick_kernels((int)table.view.nv, (int)table.params.line_buckets,
-                                         (int)table.view.bucket_bits);
+                                         (int)table.view.bucket_bits, (int)table.params.group_lanes);
   if (!ks.persistent) return HT_ERR_INVALID;
   VSS_CUDA_TRY(cudaFuncSetAttribute(ks.persistent, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)smem));

@@ -95,7 +95,7 @@ __device__ __forceinline__ SModel load_model_smem(const ReachDev& rd, int* sm) {
 // One level: a warp takes `spw` consecutive frontier states per round (spw
 // shrinks on small levels so that every warp gets work) and expands them with
 // expand_round.
-template <int NV, int L, int BW, bool TR = false>
+template <int NV, int L, int BW, bool TR = false, int G = 1>
 __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, const uint4* cur,
                                           uint32_t n_cur, uint32_t* cursor, uint4* next,
                                           uint32_t* next_count, uint32_t cap, Acc& acc,
@@ -126,7 +126,7 @@ __device__ __forceinline__ void run_level(const TableView& t, const SModel& m, c
       if (first) continue;
       break;
     }
-    expand_round<NV, L, false, TR, BW>(t, m, cur, n_cur, base, spw, next, next_count, cap, acc, lc,
+    expand_round<NV, L, false, TR, BW, G>(t, m, cur, n_cur, base, spw, next, next_count, cap, acc, lc,
                                        wsm, tr);
   }
 }
@@ -215,7 +215,7 @@ static __device__ bool grid_barrier(const ReachDev& rd, DevCounters* ctr, uint32
   return ok != 0;
 }
 
-template <int NV, int L, int BW, bool TR>
+template <int NV, int L, int BW, bool TR, int G = 1>
 __global__ void __launch_bounds__(256, reach_min_blocks<NV>()) k_reach_persistent(TableView t, ReachDev rd) {
   extern __shared__ int smem[];
   const SModel m = load_model_smem(rd, smem);
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256, reach_min_blocks<NV>()) k_reach_persisten
         tr.first_deadlock = &rd.tot->first_deadlock;
         tr.level = k;
       }
-      run_level<NV, L, BW, TR>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next,
+      run_level<NV, L, BW, TR, G>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next,
                            &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc, wsm, &tr);
       if (blockIdx.x == 0 && threadIdx.x == 0) {
         st_relaxed(&rd.tot->counts[(k + 2) % 3], 0u);
@@ -279,7 +279,7 @@ __global__ void k_reach_seed(TableView t, ReachDev rd) {
   if (acc.stored) atomicAdd(&t.ctr->stored, acc.stored);
 }
 
-template <int NV, int L, int BW>
+template <int NV, int L, int BW, int G = 1>
 __global__ void __launch_bounds__(256, reach_min_blocks<NV>()) k_reach_level(TableView t, ReachDev rd, uint32_t k) {
   extern __shared__ int smem[];
   const SModel m = load_model_smem(rd, smem);
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256, reach_min_blocks<NV>()) k_reach_level(Tab
   const uint32_t n_cur = rd.tot->counts[k % 3];
   const uint4* cur = (k & 1) ? rd.frontier1 : rd.frontier0;
   uint4* next = (k & 1) ? rd.frontier0 : rd.frontier1;
-  run_level<NV, L, BW>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next,
+  run_level<NV, L, BW, false, G>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next,
                        &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc, wsm);
   flush_acc(t, rd, acc, lc);
 }
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(256, reach_min_blocks<NV>()) k_reach_level(Tab
 // level's cursor.  A level whose frontier is empty (the search ended before
 // it) or that comes after an error returns at once; an active level records
 // its size before expanding.
-template <int NV, int L, int BW>
+template <int NV, int L, int BW, int G = 1>
 __global__ void __launch_bounds__(256, reach_min_blocks<NV>()) k_reach_step(TableView t, ReachDev rd, uint32_t k) {
   const uint32_t n_cur = ld_relaxed(&rd.tot->counts[k % 3]);
   if (n_cur == 0 || ld_relaxed(&t.ctr->err) != 0) return;
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256, reach_min_blocks<NV>()) k_reach_step(Tabl
   LocalCounters lc;
   const uint4* cur = (k & 1) ? rd.frontier1 : rd.frontier0;
   uint4* next = (k & 1) ? rd.frontier0 : rd.frontier1;
-  run_level<NV, L, BW>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next,
+  run_level<NV, L, BW, false, G>(t, m, cur, n_cur, &rd.tot->cursor[k % 3], next,
                        &rd.tot->counts[(k + 1) % 3], rd.cap, acc, lc, wsm);
   flush_acc(t, rd, acc, lc);
 }
@@ -336,14 +336,24 @@ struct ReachKernels {
   void (*step)(TableView, ReachDev, uint32_t);  // graph driver's level
 };
 
-template <int NV, int L, int BW>
+template <int NV, int L, int BW, int G = 1>
 static ReachKernels kernels_for() {
   // tracing is compiled for the default line of each bucket width only (32
-  // buckets of 32 bits, 16 of 16 bits)
-  constexpr bool kTrace = (BW == 32 ? L == 32 : L == 16);
-  return {k_reach_persistent<NV, L, BW, false>,
-          kTrace ? k_reach_persistent<NV, L, BW, kTrace> : nullptr, k_reach_seed<NV, L, BW>,
-          k_reach_level<NV, L, BW>, k_reach_step<NV, L, BW>};
+  // buckets of 32 bits, 16 of 16 bits), with one lane per successor
+  constexpr bool kTrace = G == 1 && (BW == 32 ? L == 32 : L == 16);
+  return {k_reach_persistent<NV, L, BW, false, G>,
+          kTrace ? k_reach_persistent<NV, L, BW, kTrace, G> : nullptr, k_reach_seed<NV, L, BW>,
+          k_reach_level<NV, L, BW, G>, k_reach_step<NV, L, BW, G>};
+}
+
+// Cooperative probing (ht_params.group_lanes = G): lines of 4G 32-bit buckets.
+template <int NV>
+static ReachKernels kernels_group(int G) {
+  switch (G) {
+    case 2: return kernels_for<NV, 8, 32, 2>();
+    case 4: return kernels_for<NV, 16, 32, 4>();
+    default: return kernels_for<NV, 32, 32, 8>();
+  }
 }
 
 template <int NV>
@@ -364,5 +374,6 @@ static ReachKernels kernels_w16(int L) {
 bool reach_kernels_w32_lo(int nv, int L, ReachKernels* out);  // nv 1..4
 bool reach_kernels_w32_hi(int nv, int L, ReachKernels* out);  // nv 5..8
 bool reach_kernels_w16(int nv, int L, ReachKernels* out);     // nv 1..8
+bool reach_kernels_group(int nv, int G, ReachKernels* out);   // nv 1..8, G 2 / 4 / 8
 
 }  // namespace vss

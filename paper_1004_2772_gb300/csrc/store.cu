@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) k_find_or_put_group(TableView t, const in
   if (lane == 0) {
     if (s) atomicAdd(&t.ctr->stored, (unsigned long long)s);
     if (bw) atomicAdd(&t.ctr->busy_waits, (unsigned long long)bw);
-    if (rh) atomicAdd(&t.ctr->rehashes, (unsigned long long)(rh / G));
+    if (rh) atomicAdd(&t.ctr->rehashes, (unsigned long long)rh);
   }
 }
 

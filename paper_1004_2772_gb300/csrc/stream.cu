@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) k_find_or_put_stream_group(TableView t, S
     }
     if (dig) atomicAdd(out + 1, dig);
     if (bw) atomicAdd(&t.ctr->busy_waits, (unsigned long long)bw);
-    if (rh) atomicAdd(&t.ctr->rehashes, (unsigned long long)(rh / G));
+    if (rh) atomicAdd(&t.ctr->rehashes, (unsigned long long)rh);
   }
 }
 

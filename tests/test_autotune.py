@@ -18,7 +18,9 @@ def test_candidates_respect_line_lengths_per_width():
             assert c["dedup"] == 0
     assert len({tuple(sorted(c.items())) for c in cands}) == len(cands)
     reach = list(autotune._candidates(autotune.REACH_SPACE))
-    assert len(reach) == (3 + 2) * 2
+    # one lane per successor: 32-bit 3 lines + 16-bit 2; groups of 2, 4, 8: one line each
+    assert len(reach) == (3 + 2 + 3) * 2
+    assert all(c["line_buckets"] == 4 * c["group_lanes"] for c in reach if c["group_lanes"] > 1)
     probe = list(autotune._candidates(autotune.PROBE_SPACE))
     assert len(probe) == 2 * 3 and {"rehash": 1, "max_rehash": 16} in probe
 

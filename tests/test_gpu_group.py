@@ -88,4 +88,67 @@ def test_group_parameters_validated(cuda_lib):
     with pytest.raises(cuda_lib.HtError):
         cuda_lib.Table(10, 4, group_lanes=4, bucket_bits=16)
     with pytest.raises(cuda_lib.HtError):
-        cuda_lib.ReachContext(10, 4, group_lanes=4)
+        cuda_lib.ReachContext(10, 4, group_lanes=4, line_buckets=32)
+    # tracing is compiled for one lane per successor only
+    ctx = cuda_lib.ReachContext(18, 5, group_lanes=4)
+    got = ctx.reach(synth.tiny_interleaving_model(), mode=cuda_lib.REACH_PERSISTENT | cuda_lib.REACH_TRACE,
+                    raise_on_error=False)
+    assert got.status == cuda_lib.HT_ERR_INVALID
+    # the many-model kernels take one lane per key
+    with pytest.raises(cuda_lib.HtError):
+        cuda_lib.ReachBatch([synth.tiny_interleaving_model()], group_lanes=4)
+
+
+# ---------------------------------------------------------------------------
+# Reachability with cooperative probing: the G lanes of a group build the same
+# successor and walk its line of 4G buckets together.
+# ---------------------------------------------------------------------------
+
+def _reach_check(cuda_lib, ctx, m, mode, ref):
+    from test_gpu_reach import check
+    return check(cuda_lib, ctx, m, mode, ref)
+
+
+@pytest.mark.parametrize("G", GROUPS)
+def test_reach_with_groups_tiny_and_guarded(cuda_lib, G):
+    """The tiny interleaving model (rows of 5 words) and guarded models with
+    rows of 13, 16 and 32 words, in all three drivers."""
+    from test_gpu_reach import MODES, log2_for
+    cases = [(synth.tiny_interleaving_model(), 18)]
+    for W in (13, 16, 32):
+        cases.append((synth.beem_shaped_model(13, n_procs=10, n_shared=3, state_words=W, n_lo=3, n_hi=6,
+                                              update_pct=40), None))
+    for m, lg in cases:
+        ref = oracle.reach(m)
+        ctx = cuda_lib.ReachContext(lg or log2_for(ref.states), m.state_words, max_levels=4096,
+                                    group_lanes=G)
+        for mode in MODES:
+            _reach_check(cuda_lib, ctx, m, mode, ref)
+        ctx.close()
+
+
+@pytest.mark.parametrize("G", GROUPS)
+def test_reach_with_groups_high_load_prime_lines(cuda_lib, G):
+    """A table of a prime number of lines at load 0.9: walks rehash."""
+    m = synth.beem_shaped_model(13, n_procs=10, n_shared=3, state_words=16, n_lo=3, n_hi=6, update_pct=40)
+    ref = oracle.reach(m)
+    lines = {8: 2113, 4: 4229, 2: 8461}[G]                      # primes: load 0.90 with 4G-bucket lines
+    ctx = cuda_lib.ReachContext(None, 16, n_buckets=4 * G * lines, max_levels=4096, group_lanes=G)
+    got = _reach_check(cuda_lib, ctx, m, 0, ref)
+    assert got.rehashes > 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("G", [4, 8])
+def test_reach_with_groups_medium_golden(cuda_lib, G):
+    """The 5.5M-state BEEM-shaped medium model against its stored values."""
+    from conftest import load_golden
+    g = load_golden("beem_medium.json")
+    m = synth.beem_shaped_model(seed=7, update_pct=40)
+    ctx = cuda_lib.ReachContext(24, 16, max_levels=4096, group_lanes=G)
+    r = ctx.reach(m)
+    assert (r.states, r.transitions, r.deadlocks, r.digest, r.level_sizes) == (
+        g["states"], g["transitions"], g["deadlocks"], int(g["digest"], 16), g["level_sizes"])
+    done, writing, digest = ctx.scan()
+    assert (done, writing, digest) == (g["states"], 0, r.digest)
+    ctx.close()
