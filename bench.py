@@ -150,7 +150,8 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "clocks.mem,temperature.gpu,pci.bus_id")
 
     def __init__(self, gpu_index: int):
         vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
@@ -185,6 +186,8 @@ class ClockSampler:
 
     def summary(self):
         sm, mx, reasons = [], None, set()
+        extra = {"power_w": [], "mem_mhz": [], "temp_c": []}
+        bus = None
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [x.strip() for x in ln.split(",")]
@@ -198,11 +201,24 @@ class ClockSampler:
             for n, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(n)
+            for key, i in (("power_w", 3), ("mem_mhz", 9), ("temp_c", 10)):
+                try:
+                    extra[key].append(float(parts[i]))
+                except (ValueError, IndexError):
+                    pass
+            if len(parts) > 11:
+                bus = parts[11]
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         sm.sort()
-        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        out = {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+               "samples": len(sm)}
+        for key, vals in extra.items():  # medians, for comparing runs across boxes
+            if vals:
+                out[key] = sorted(vals)[len(vals) // 2]
+        if bus:
+            out["pci_bus_id"] = bus
+        return out
 
 
 def algorithmic_bytes(states, transitions, state_words=16):
