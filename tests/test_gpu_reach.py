@@ -80,6 +80,21 @@ def test_guarded_model_row_shapes(cuda_lib, W):
         check(cuda_lib, ctx, m, mode, ref)
 
 
+@pytest.mark.parametrize("W", [13, 16, 20, 24, 28, 32])
+def test_guarded_model_every_row_width(cuda_lib, W):
+    """A guarded model of 60,837 states and 35 levels with rows of 4 to 8
+    16-byte chunks (every compiled row width from 13 words up), in all three
+    drivers: many warp rounds per level and a table of 2^17 buckets (two
+    blocks per SM)."""
+    m = synth.beem_shaped_model(13, n_procs=10, n_shared=3, state_words=W, n_lo=3, n_hi=6,
+                                update_pct=40)
+    ref = oracle.reach(m)
+    assert ref.states == 60837
+    ctx = cuda_lib.ReachContext(log2_for(ref.states), W, max_levels=4096)
+    for mode in MODES:
+        check(cuda_lib, ctx, m, mode, ref)
+
+
 @pytest.mark.parametrize("P,W", [(16, 16), (24, 24), (31, 32)])
 def test_rounds_with_more_successors_than_descriptors(cuda_lib, P, W):
     """Every state has 2P successors (32, 48 or 62); a round holds
