@@ -79,6 +79,13 @@ def test_clock_summary_parses_nvidia_smi_lines():
     s = c.summary()
     assert s["sm_max_mhz"] == 2070.0 and s["samples"] == 2
     assert s["reasons"] == ["sw_power_cap"]
+    # the wider query: memory clock, temperature and bus id as medians / last seen
+    c.lines = ["0, 2070, 2070, 441.2, 0x0, Not Active, Not Active, Not Active, Not Active, 3996, 30, 0:07.0",
+               "0, 2070, 2070, 460.0, 0x0, Not Active, Not Active, Not Active, Not Active, 3996, 31, 0:07.0",
+               "0, 2070, 2070, 455.5, 0x0, Not Active, Not Active, Not Active, Not Active, [N/A], 32, 0:07.0"]
+    s = c.summary()
+    assert s["reasons"] == [] and s["samples"] == 3
+    assert (s["power_w"], s["mem_mhz"], s["temp_c"], s["pci_bus_id"]) == (455.5, 3996.0, 31.0, "0:07.0")
 
 
 def test_reference_arm_prints_one_json_line():
