@@ -63,3 +63,15 @@ def test_no_alloc_16_bit_buckets(cuda_lib):
     ref = oracle.reach(m)
     st, r, levels = b.reach_noalloc(m, 18, b.make_params(bucket_bits=16), max_levels=4096)
     _same(st, r, levels, ref)
+
+
+@pytest.mark.parametrize("G", [2, 8])
+def test_no_alloc_with_lane_groups(cuda_lib, G):
+    """Cooperative probing (groups of G lanes, lines of 4G buckets) through
+    the fixed array too."""
+    b = cuda_lib
+    m = synth.tiny_interleaving_model()
+    ref = oracle.reach(m)
+    st, r, levels = b.reach_noalloc(m, 18, b.make_params(group_lanes=G, line_buckets=4 * G),
+                                    max_levels=4096)
+    _same(st, r, levels, ref)
