@@ -199,11 +199,12 @@ ht_status ht_arrays(ht_t* h, uint32_t** buckets_dev, int32_t** data_dev, uint32_
 
 /* A fill with n_ids distinct keys is a stream of 2*n_ids calls: call 2i is key
  * i; call 2i+1 repeats a key drawn from r = mix(c ^ mix(seed)) -- uniformly
- * from ids [0, i] when zipf_table_dev is NULL, else from ranks 1..n_ids of a
- * Zipf quantile table (65537 uint32 entries: a cell from the top 16 bits of r,
- * a rank uniform inside the cell).  Key i: word 0 = MurmurHash3 fmix32(i),
- * word j >= 1 = low 32 bits of mix((seed << 36) + (i << 4) + j), mix = one
- * SplitMix64 output step.
+ * from ids [0, i] as floor(r * (i + 1) / 2^64) when zipf_table_dev is NULL,
+ * else from ranks 1..n_ids of a Zipf quantile table (65537 uint32 entries: a
+ * cell from the top 16 bits of r, a rank uniform inside the cell).  Key i:
+ * word 0 = MurmurHash3 fmix32(i); words 2q-1 and 2q (q >= 1) = the low and
+ * high 32 bits of mix((seed << 36) + (i << 4) + q), mix = one SplitMix64
+ * output step.
  * vss_gen_keys writes calls [call_begin, call_begin + n_calls) as rows of
  * state_words int32 to keys_dev.  Enqueued on stream. */
 ht_status vss_gen_keys(uint64_t seed, uint64_t n_ids, uint64_t call_begin, uint64_t n_calls,

@@ -2,15 +2,17 @@
 //
 // A fill of a table with n_ids distinct keys is a stream of 2 * n_ids calls:
 // call 2i inserts key i; call 2i+1 repeats a key chosen from
-// r = mix(c xor mix(seed)): uniformly among the earlier ids [0, i], or by a
+// r = mix(c xor mix(seed)): uniformly among the earlier ids [0, i] as
+// floor(r * (i + 1) / 2^64) (a multiply-high range reduction), or by a
 // Zipf(1.1) law over all ids through an integer quantile table (so that the
 // device and the host generator draw identical ids).  Key i is
 //   word 0      = fmix32(i)                     (MurmurHash3 finaliser: a bijection,
 //                                                so distinct ids give distinct keys)
-//   word j >= 1 = low 32 bits of mix((seed << 36) + (i << 4) + j)
-// with mix the SplitMix64 output step (Steele, Lea, Flood 2014).  These are
-// inputs, not part of the method: the same definition is implemented on the
-// host by the seeded input generator, and a GPU test checks the two agree.
+//   words 2q-1, 2q (q >= 1) = the low and high 32 bits of mix((seed << 36) + (i << 4) + q)
+// with mix the SplitMix64 output step (Steele, Lea, Flood 2014): one output
+// per two words.  These are inputs, not part of the method: the same
+// definition is implemented on the host by the seeded input generator, and a
+// GPU test checks the two agree.
 //
 // k_gen_keys materialises keys (for the batch API); k_find_or_put_stream
 // runs find-or-put on keys generated in registers, so the table is measured
@@ -48,7 +50,7 @@ __device__ __forceinline__ uint64_t call_id(const StreamSpec& s, uint64_t c) {
   const uint64_t i = c >> 1;
   if (!(c & 1)) return i;
   const uint64_t r = sm_out(c ^ s.seed_key);
-  if (!s.zipf) return r % (i + 1);
+  if (!s.zipf) return __umul64hi(r, i + 1);
   const uint32_t cell = (uint32_t)(r >> 48);
   const uint64_t lo = s.zipf[cell], hi = s.zipf[cell + 1];
   const uint64_t width = hi > lo ? hi - lo : 1;
@@ -60,10 +62,16 @@ __device__ __forceinline__ uint64_t call_id(const StreamSpec& s, uint64_t c) {
 template <int NV>
 __device__ __forceinline__ void key_of(uint64_t seed, uint64_t id, uint32_t W, Vec<NV>& k) {
   const uint64_t base = (seed << 36) + (id << 4);
-  uint32_t w[4 * NV];
+  uint32_t w[4 * NV + 1];
+  w[0] = fmix32((uint32_t)id);
 #pragma unroll
-  for (int j = 0; j < 4 * NV; ++j)
-    w[j] = (j >= (int)W) ? 0u : (j == 0 ? fmix32((uint32_t)id) : (uint32_t)sm_out(base + j));
+  for (int q = 1; 2 * q - 1 < 4 * NV; ++q) {  // words 2q-1 and 2q from one output
+    const uint64_t z = sm_out(base + (uint64_t)q);
+    w[2 * q - 1] = (uint32_t)z;
+    w[2 * q] = (uint32_t)(z >> 32);
+  }
+#pragma unroll
+  for (int j = 0; j < 4 * NV; ++j) w[j] = j < (int)W ? w[j] : 0u;
 #pragma unroll
   for (int q = 0; q < NV; ++q) k.c[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
 }

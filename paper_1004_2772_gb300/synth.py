@@ -276,16 +276,32 @@ def _fmix32(x: np.ndarray) -> np.ndarray:
 
 
 def key_words(seed: int, ids: np.ndarray, state_words: int = 16) -> np.ndarray:
-    """Key of each id: word 0 = fmix32(id) (distinct ids give distinct keys),
-    word j >= 1 = low 32 bits of mix((seed << 36) + (id << 4) + j)."""
+    """Key of each id: word 0 = fmix32(id) (distinct ids give distinct keys);
+    words 2q-1 and 2q (q >= 1) = the low and high 32 bits of
+    mix((seed << 36) + (id << 4) + q), one SplitMix64 output per two words."""
     ids = np.asarray(ids, dtype=np.uint64)
     out = np.empty((ids.shape[0], state_words), dtype=np.uint32)
     out[:, 0] = _fmix32(ids.astype(np.uint32))
     base = (np.uint64((seed << 36) & MASK64) + (ids << np.uint64(4)))
-    for j in range(1, state_words):
+    for q in range(1, (state_words + 1) // 2 + 1):
         with np.errstate(over="ignore"):
-            out[:, j] = (_mix_u64(base + np.uint64(j)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+            z = _mix_u64(base + np.uint64(q))
+        for j, part in ((2 * q - 1, z & np.uint64(0xFFFFFFFF)), (2 * q, z >> np.uint64(32))):
+            if j < state_words:
+                out[:, j] = part.astype(np.uint32)
     return out.view(np.int32)
+
+
+def mulhi_range(r: np.ndarray, n: np.ndarray) -> np.ndarray:
+    """floor(r * n / 2^64) for uint64 r and 1 <= n < 2^32 (a multiply-high
+    range reduction of r onto [0, n)), exactly, in 64-bit arithmetic."""
+    r = np.asarray(r, dtype=np.uint64)
+    n = np.asarray(n, dtype=np.uint64)
+    lo32 = np.uint64(0xFFFFFFFF)
+    with np.errstate(over="ignore"):
+        hi = (r >> np.uint64(32)) * n
+        lo = (r & lo32) * n
+        return (hi + (lo >> np.uint64(32))) >> np.uint64(32)
 
 
 ZIPF_CELLS = 1 << 16
@@ -313,7 +329,8 @@ def call_ids(seed: int, n_ids: int, start: int, count: int, dist: str = "uniform
              table: np.ndarray | None = None) -> np.ndarray:
     """Key ids of calls start .. start+count of a fill with n_ids distinct keys
     and 2 * n_ids calls.  Call 2i inserts id i; call 2i+1 repeats an id drawn
-    from r = mix(mix(seed) ^ c): uniform over [0, i] ('an earlier key'), or
+    from r = mix(mix(seed) ^ c): uniform over [0, i] ('an earlier key', as
+    floor(r * (i + 1) / 2^64)), or
     Zipf over ranks 1..n_ids (id = rank - 1, id 0 hottest) through the
     quantile table.  So half the calls are duplicates and exactly n_ids keys
     are distinct."""
@@ -323,7 +340,7 @@ def call_ids(seed: int, n_ids: int, start: int, count: int, dist: str = "uniform
     key = np.uint64(splitmix64_mix(seed & MASK64))
     r = _mix_u64(c ^ key)
     if dist == "uniform":
-        dup = r % (i + np.uint64(1))
+        dup = mulhi_range(r, i + np.uint64(1))
     elif dist == "zipf":
         assert table is not None and table.shape[0] == ZIPF_CELLS + 1
         cell = (r >> np.uint64(48)).astype(np.int64)
