@@ -273,6 +273,49 @@ def test_deadlock_trace(cuda_lib, which):
     _check_trace(m, level, path, ref)
 
 
+@pytest.mark.parametrize("which", ["tiny0", "medium"])
+def test_deadlock_trace_16_bit_buckets(cuda_lib, which):
+    """Tracing with 16-bit buckets (its default 16-bucket line): the same
+    shortest-path trace properties, and the run itself bit-exact."""
+    if which == "medium":
+        g = load_golden("beem_medium.json")
+        m = synth.beem_shaped_model(**g["model"])
+        lg = g["log2_buckets"]
+    else:
+        kws = [kw for kw in TINY_BEEM if oracle.reach(synth.beem_shaped_model(**kw)).deadlocks > 0]
+        m = synth.beem_shaped_model(**kws[0])
+        lg = 12
+    ref = oracle.reach(m)
+    assert ref.deadlocks > 0
+    ctx = cuda_lib.ReachContext(lg, m.state_words, max_levels=4096, bucket_bits=16)
+    got = ctx.reach(m, mode=cuda_lib.REACH_PERSISTENT | cuda_lib.REACH_TRACE)
+    assert (got.states, got.transitions, got.deadlocks, got.digest, got.level_sizes) == (
+        ref.states, ref.transitions, ref.deadlocks, ref.digest, ref.level_sizes)
+    level, path = ctx.deadlock_trace()
+    _check_trace(m, level, path, ref)
+
+
+@pytest.mark.parametrize("which", ["tiny1", "medium"])
+def test_deadlock_trace_prime_line_table(cuda_lib, which):
+    """Tracing in a table of a prime number of 32-bucket lines (division by
+    the line count instead of a mask): 131 lines for a tiny guarded model,
+    2^19 - 1 lines (load 0.33) for the medium model."""
+    if which == "medium":
+        m = synth.beem_shaped_model(**load_golden("beem_medium.json")["model"])
+        lines = (1 << 19) - 1
+    else:
+        kws = [kw for kw in TINY_BEEM if oracle.reach(synth.beem_shaped_model(**kw)).deadlocks > 0]
+        m = synth.beem_shaped_model(**kws[1])
+        lines = 131
+    ref = oracle.reach(m)
+    ctx = cuda_lib.ReachContext(None, m.state_words, n_buckets=32 * lines, max_levels=4096)
+    got = ctx.reach(m, mode=cuda_lib.REACH_PERSISTENT | cuda_lib.REACH_TRACE)
+    assert (got.states, got.transitions, got.deadlocks, got.digest, got.level_sizes) == (
+        ref.states, ref.transitions, ref.deadlocks, ref.digest, ref.level_sizes)
+    level, path = ctx.deadlock_trace()
+    _check_trace(m, level, path, ref)
+
+
 def test_no_deadlock_no_trace(cuda_lib):
     m = synth.tiny_interleaving_model()
     ctx = cuda_lib.ReachContext(18, 5, max_levels=256)
