@@ -361,7 +361,7 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="hashtable: tune parameters first")
     ap.add_argument("--duration", type=float, default=10.0, help="serve: seconds of arrivals")
     ap.add_argument("--models", type=int, default=256, help="batch: number of models")
-    ap.add_argument("--probe-gib", type=float, default=16.0, help="probe-sweep: buffer size (GiB)")
+    ap.add_argument("--probe-gib", type=float, default=16.0, help="buffer size (GiB) of the random-access probe every workload runs for its roofline")
     ap.add_argument("--probe-modes", default="0,1,2,3,4,5,6,7,8,9,10,11,12", help="probe-sweep: modes")
     ap.add_argument("--probe-default-shape", action="store_true",
                     help="probe-sweep: only the default shape (8 in flight, 8 blocks/SM, 256 threads)")
